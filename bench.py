@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the colour-coding hot path on one GB300 (or N replicas).
+
+Workload: Chung-Lu power-law graph, n = 1M, m ~ 10M, degree exponent 2.5,
+largest expected degree 10k (synthetic, seeded); k = 5 colours, 64-bit
+counts.  One step = colour the graph, build the exact count tables for
+h = 1..5 (neighbour sums + merges), prefix the level totals, draw 1M uniform
+colourful 5-treelets, classify their induced 5-graphlets and estimate the
+21 graphlet counts -- every step of the path, through the C ABI.
+
+value: DP table entries (n x live entries per node) per second of step time.
+Also reported: samples/s, per-phase and per-kernel device times, the
+roofline of the dominant kernel, an end-to-end number through host buffers,
+the CPU oracle as a baseline, and SM clocks sampled during the timed region.
+
+Multi-GPU: one process per GPU (torchrun); every rank builds and samples its
+own colouring of the same graph (independent replicas, no data-path
+collective), so per-GPU work is fixed as N grows ("weak").  --impl reference
+times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+K = 5
+BITS = 64
+SAMPLES = 1_000_000
+R_H = [0, 1, 1, 2, 4, 9, 20, 48, 115]  # rooted shapes per size
+
+
+def workload_graph(small: bool):
+    if small:
+        return synth.er_1k(), "er_1k"
+    return synth.chung_lu_1m(), "chung_lu_1m_k5"
+
+
+def live_entries_per_node(k: int) -> int:
+    return sum(R_H[h] * math.comb(k - 1, h - 1) for h in range(1, k + 1))
+
+
+def geometry(k: int):
+    Bc = {h: math.comb(k - 1, h - 1) for h in range(1, k + 1)}
+    Bs = {h: math.comb(k - 1, h) for h in range(1, k)}
+    Wc = {h: R_H[h] * Bc[h] for h in Bc}
+    Ws = {h: R_H[h] * Bs[h] for h in Bs}
+    return Wc, Ws
+
+
+def algorithmic_bytes(name: str, n: int, nnz: int, k: int, B: int):
+    """Compulsory DRAM bytes of one launch of a build kernel (each input row
+    read once, each output row written once, plus the CSR it walks)."""
+    Wc, Ws = geometry(k)
+    csr = 8 * (n + 1) + 4 * nnz + n
+    if name == "gather_h1":
+        return csr + n * (k - 1) * B
+    if name.startswith("gather_h"):
+        h = int(name[len("gather_h"):])
+        return n * Wc[h] * B + n * Ws[h] * B + csr
+    if name.startswith("merge_h"):
+        from oracle import catalog as cat  # shape sizes only (catalogue, no arithmetic)
+        h = int(name[len("merge_h"):])
+        c = cat.Catalog(k)
+        used1, used2 = set(), set()
+        for g in range(c.first[h], c.first[h + 1]):
+            used1.add(c.size[c.left[g]])
+            used2.add(c.size[c.right[g]])
+        rd = sum(Wc[x] for x in used1 if x > 1) + sum(Ws[x] for x in used2)
+        return n * (rd + Wc[h]) * B
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int):
+    """Time the oracle on the workload: its table build on the full graph
+    plus n_samples uniform samples with classification; the sampling time
+    is scaled to the step's 1M samples."""
+    import oracle
+    oracle.build()
+    oracle.class_codes(k)  # class list precomputed outside the timing
+    oracle.sigma(k)
+    colors = oracle.color(graph.n, k, seed)
+    t0 = time.perf_counter()
+    T = oracle.Tables(graph, colors, k, BITS, nthreads=threads)
+    t1 = time.perf_counter()
+    T.estimate_uniform(k, seed=seed, n_samples=n_samples)
+    t2 = time.perf_counter()
+    build_s, samp_s = t1 - t0, t2 - t1
+    step_s = build_s + samp_s * (SAMPLES / n_samples)
+    entries = graph.n * live_entries_per_node(k)
+    return {"value": entries / step_s, "build_s": build_s, "sample_s": samp_s,
+            "step_s_equiv": step_s}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    graph, wname = workload_graph(args.small)
+    threads = os.cpu_count() or 1
+    n_samp = 1000 if not args.small else 10_000
+    # warm-up: the oracle on a small graph of the same family
+    warm = synth.chung_lu_scaled(5000, seed=1)
+    for i in range(args.warmup):
+        oracle_step_rate(warm, K, 100, 100 + i, threads)
+    res = [oracle_step_rate(graph, K if not args.small else 4, n_samp, 10 + i, threads)
+           for i in range(args.steps)]
+    val = statistics.median(r["value"] for r in res)
+    step_ms = statistics.median(r["step_s_equiv"] for r in res) * 1e3
+    sample = (f"oracle build of the full {wname} graph plus {n_samp} samples per step; "
+              f"sampling time scaled to {SAMPLES} samples")
+    line = {
+        "impl": "reference", "metric": "DP table entries/s", "value": val,
+        "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": wname, "k": K, "count_bits": BITS, "samples_per_step": SAMPLES},
+        "cpu_baseline": {"value": val, "unit": "entries/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2009_03052_gb300 as M
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    M.build()
+    M.load()
+    graph, wname = workload_graph(args.small)
+    k = 4 if args.small else K
+    samples = 10_000 if args.small else SAMPLES
+    n, nnz = graph.n, graph.nnz
+    G = M.Graph.from_csr(graph)
+    colbuf = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    phase = {"build": [], "sample": []}
+
+    def step(seed: int, record: bool):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        col = M.color(G, k, seed, out=colbuf)
+        T = M.Tables(G, col, k, BITS)
+        e1.record(stream)
+        est, hits, _ = T.estimate(k, seed=seed, samples=samples)
+        e2.record(stream)
+        T.free()
+        if record:
+            e2.synchronize()
+            phase["build"].append(e0.elapsed_time(e1))
+            phase["sample"].append(e1.elapsed_time(e2))
+        return hits
+
+    seed0 = 1000 * rank
+    for i in range(args.warmup):
+        step(seed0 + i, False)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (126 MB)
+
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    M.profile_reset()
+    M.profile_enable(True)
+    launches0 = M.launch_count()
+    step_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict L2 between steps, outside the step's events
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(seed0 + args.warmup + i, True)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    launches = M.launch_count() - launches0
+    prof = M.profile_read()
+    M.profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    my_total = sum(step_ms)
+    t = torch.tensor([my_total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+
+    entries = n * live_entries_per_node(k)
+    value = entries * args.steps * world / (total_ms / 1e3)
+    build_ms = statistics.mean(phase["build"])
+    sample_ms = statistics.mean(phase["sample"])
+
+    # per-kernel shares and the roofline of the dominant kernel
+    ktot = sum(v[0] for v in prof.values()) or 1.0
+    kernels = {name: {"ms": round(ms, 4), "launches": cnt, "share": round(ms / ktot, 4)}
+               for name, (ms, cnt) in sorted(prof.items(), key=lambda x: -x[1][0])}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peaks = json.load(open(peaks_path))
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    modeled = [(nm, v) for nm, v in prof.items()
+               if algorithmic_bytes(nm, n, nnz, k, BITS // 8) is not None]
+    roof = None
+    if modeled:
+        nm, (ms, cnt) = max(modeled, key=lambda x: x[1][0])
+        by = algorithmic_bytes(nm, n, nnz, k, BITS // 8)
+        achieved = by / (ms / cnt / 1e3) / 1e9
+        traffic = TRAFFIC.get((wname, nm))
+        roof = {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": traffic, "algorithmic_bytes": by, "peak_source": peak_src,
+                "avg_launch_ms": round(ms / cnt, 4)}
+    top = max(prof.items(), key=lambda x: x[1][0])[0] if prof else None
+
+    # end to end through the C ABI with host buffers: graph upload, colour,
+    # build, sample, estimates copied back
+    e2e_ms = []
+    h2d = graph.row_ptr.nbytes + graph.col.nbytes
+    d2h = 0
+    for i in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = M.Graph(graph.row_ptr, graph.col, trusted=True)
+        col = M.color(G2, k, seed0 + 77 + i, out=colbuf)
+        T2 = M.Tables(G2, col, k, BITS)
+        est, hits, _ = T2.estimate(k, seed=seed0 + 77 + i, samples=samples)
+        d2h = est.nbytes + hits.nbytes
+        T2.free()
+        G2.free()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = entries * world / (float(e2e_t.item()) / 1e3)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        n_samp = 1000 if not args.small else 10_000
+        r = oracle_step_rate(graph, k, n_samp, 5, threads)
+        cpu = {"value": r["value"], "unit": "entries/s", "cores": threads, "kind": "oracle",
+               "sample": (f"oracle build of the full {wname} graph ({r['build_s']:.1f} s) plus "
+                          f"{n_samp} samples ({r['sample_s']:.2f} s), sampling scaled to "
+                          f"{samples} samples per step")}
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": "DP table entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wname, "n": n, "m": nnz // 2, "k": k, "count_bits": BITS,
+                   "samples_per_step": samples, "l2": "flushed between steps (256 MiB write, "
+                   "outside the per-step events)", "parallelism": f"replicas{world}"},
+        "samples_per_s": samples * args.steps * world / (total_ms / 1e3),
+        "phases_ms": {"build": round(build_ms, 3), "sample_classify_estimate": round(sample_ms, 3)},
+        "build_entries_per_s": entries / (build_ms / 1e3),
+        "roofline": roof, "top_kernel": top, "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.median(e2e_ms)},
+        "cpu_baseline": cpu, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from
+# one ncu capture of the named kernel on the named workload; None when the
+# kernel changed since the capture.
+TRAFFIC: dict = {}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--small", action="store_true", help="the 1k-node ER case (k = 4)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

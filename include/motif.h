@@ -1,0 +1,219 @@
+/*
+ * motif.h -- C ABI of the GB300 colour-coding motif library (libmotif).
+ *
+ * Colour coding for k-node graphlet counting after Bressan, Leucci and
+ * Panconesi, "Faster motif counting via succinct color coding and adaptive
+ * sampling": colour the graph (Section 2.1), build the exact colourful
+ * treelet count tables c(T_C, v) by the dynamic program of Eq. (1), sample
+ * colourful treelets uniformly (Section 2.2) or adaptively (Algorithm AGS,
+ * Section 4.1), classify the induced graphlets (Section 4.3.3) and estimate
+ * graphlet counts.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" must point to device memory of the current CUDA
+ *    device; "host" pointers to host memory.  The caller owns every pointer it
+ *    passes; the library owns the handles it returns and frees them in
+ *    mc_free_*.  Device work is queued on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  Entry points that return host results
+ *    synchronise `stream` before returning.
+ *  - Every entry point returns an mc_status.  On error no handle is returned,
+ *    nothing the caller owns is freed, and mc_last_error() (per host thread)
+ *    says why.  No C++ exception crosses the ABI.
+ *  - Counts are exact unsigned integers of 64 or 128 bits.  An intermediate
+ *    value that does not fit the count width (a table entry, a neighbour sum,
+ *    a merge numerator or a level total) makes the call fail with
+ *    MC_E_OVERFLOW; nothing wraps.
+ *  - Graphs are simple and undirected (Section 1.2): n < 2^32 nodes, CSR with
+ *    symmetric, sorted, duplicate-free, loop-free adjacency lists.
+ *  - 2 <= k <= 8 colours; treelets and graphlets have h <= k nodes.
+ */
+#ifndef MOTIF_H
+#define MOTIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MC_OK = 0,
+    MC_E_INVALID = 1,      /* bad argument or malformed graph */
+    MC_E_NOMEM = 2,        /* the allocator returned NULL */
+    MC_E_OVERFLOW = 3,     /* a count does not fit the chosen width */
+    MC_E_CUDA = 4,         /* a CUDA runtime call failed */
+    MC_E_TIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+    MC_E_UNSUPPORTED = 6,  /* valid but not supported (e.g. k > 8) */
+    MC_E_INTERNAL = 7      /* an internal consistency check failed */
+} mc_status;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes, aligned to 256 bytes, usable on `stream` (NULL on failure); free
+ * releases it.  `ctx` is passed back unchanged and must outlive every handle
+ * created with this allocator.  A NULL allocator means cudaMalloc/cudaFree. */
+typedef struct mc_allocator {
+    void *(*alloc)(size_t bytes, void *ctx, void *stream);
+    void (*free)(void *ptr, size_t bytes, void *ctx, void *stream);
+    void *ctx;
+} mc_allocator;
+
+typedef struct mc_graph mc_graph;
+typedef struct mc_tables mc_tables;
+
+/* ------------------------------------------------------------------------ */
+/* Graph                                                                     */
+/* ------------------------------------------------------------------------ */
+#define MC_GRAPH_DEVICE_PTRS 0x1u  /* row_ptr and col are device pointers */
+#define MC_GRAPH_TRUSTED     0x2u  /* skip the canonical-CSR validation */
+
+/* Copy a CSR graph to the device.  row_ptr: int64[n+1] with row_ptr[0] = 0
+ * and row_ptr[n] = nnz; col: uint32[nnz], node u's neighbours are
+ * col[row_ptr[u] .. row_ptr[u+1]) in strictly ascending order.  Unless
+ * MC_GRAPH_TRUSTED is set the copy is checked on the device (bounds, order,
+ * no loops, symmetry) and a malformed graph gives MC_E_INVALID.  The input
+ * buffers are not retained. */
+mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_ptr, const uint32_t *col,
+                        uint32_t flags, const mc_allocator *alloc, void *stream, mc_graph **out);
+void mc_free_graph(mc_graph *g);
+/* n, nnz (= 2m) and the largest degree. */
+mc_status mc_graph_info(const mc_graph *g, int64_t *n, int64_t *nnz, int64_t *max_degree);
+
+/* ------------------------------------------------------------------------ */
+/* Colouring (Section 2.1: every node draws a colour uniformly from [k])     */
+/* ------------------------------------------------------------------------ */
+/* colors: device uint8[n], written.  c_v = floor(k * x0 / 2^32) with x0 the
+ * first word of Philox4x32-10 (Salmon et al., SC 2011) at key = seed
+ * (low word first) and counter = (v, 0, 0, 0xC010). */
+mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Count tables (Section 2.1, Eq. 1; Section 3.2.1)                          */
+/* ------------------------------------------------------------------------ */
+/* Build c(T_C, v) for every rooted treelet shape T on h = 1..k nodes, every
+ * colour set C with |C| = h and every node v, by the dynamic program of
+ * Eq. (1) split in two steps per level: the neighbour sums
+ * S(T'', C'', v) = sum_{u ~ v} c(T''_{C''}, u) and the disjoint-colour merge
+ * c(T_C, v) = (1/beta_T) sum_{C' + C'' = C} c(T'_{C'}, v) S(T'', C'', v).
+ * colors: device uint8[n] with values < k (read during the call only).
+ * count_bits: 64 or 128.  flags: 0 (reserved).  The tables stay on the device
+ * until mc_free_tables; they are immutable, so concurrent readers are safe.
+ * The graph must outlive the tables. */
+mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
+                          uint32_t flags, const mc_allocator *alloc, void *stream,
+                          mc_tables **out);
+void mc_free_tables(mc_tables *t);
+
+/* Totals (the occ() queries of Section 3): rooted = sum over v and over the
+ * rooted shapes of size h (all of them when unrooted_shape < 0, else the
+ * rootings of that unrooted shape) of c(T_C, v); unrooted = rooted / h, the
+ * number of colourful h-treelet copies t (or t_j).  Host uint64[2] each,
+ * low word first.  Synchronises `stream`. */
+mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
+                   uint64_t unrooted_count[2], void *stream);
+
+/* Layout of the level-h table (which = 0: counts c, h = 1..k; which = 1:
+ * neighbour sums S, h = 1..k-1).  Row v holds row_entries entries of
+ * entry_bytes (8 or 16, little-endian, low word first).  Entry
+ * (s, rho) sits at s * B + rho, s the rooted shape id, B = C(k-1, h-1) for
+ * c and C(k-1, h) for S, and rho the colex rank of the colour set without c_v
+ * after deleting colour c_v from the palette (colours above c_v move down by
+ * one).  Only sets that contain c_v (for c) or avoid it (for S) are stored. */
+mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,
+                          int *entry_bytes);
+/* Copy a whole level (n * row_entries * entry_bytes bytes) into dst (host or
+ * device as dst_on_device says).  Level 1 of c is all ones and is produced on
+ * the fly.  Synchronises `stream`. */
+mc_status mc_read_table(const mc_tables *t, int h, int which, void *dst, size_t dst_bytes,
+                        int dst_on_device, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Sampling (Section 2.2; sample(T) of Section 4.1)                          */
+/* ------------------------------------------------------------------------ */
+/* Draw `count` colourful h-treelets (2 <= h <= k) uniformly among all
+ * copies (unrooted_shape < 0) or among the copies of one unrooted shape,
+ * with sample indices first_index, first_index + 1, ...  Sample i is a pure
+ * function of (tables, seed, i), so batches can be split or reordered freely.
+ * Outputs (device; any may be NULL): nodes uint32[count*h] (each sample's
+ * nodes ascending), roots uint32[count], shapes int32[count] (rooted shape
+ * id), classes int32[count] (id of the induced h-node graphlet: rank of its
+ * canonical adjacency word among those of all connected h-node graphs).
+ * MC_E_INVALID when no such treelet exists. */
+mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
+                    uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
+                    int32_t *shapes, int32_t *classes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Estimation (Section 2.2 uniform; Algorithm AGS, Section 4.1)              */
+/* ------------------------------------------------------------------------ */
+#define MC_EST_UNIFORM 0
+#define MC_EST_AGS 1
+
+typedef struct {
+    int mode;              /* MC_EST_UNIFORM or MC_EST_AGS */
+    int h;                 /* graphlet size, 2 <= h <= k */
+    uint64_t seed;
+    uint64_t first_index;  /* index of the first sample */
+    int64_t samples;       /* uniform: samples drawn; AGS: the most it may draw */
+    int64_t cbar;          /* AGS covering threshold; <= 0: ceil(4/eps^2 ln(2s/delta)) */
+    double eps, delta;     /* AGS accuracy, used when cbar <= 0 */
+    int64_t batch;         /* AGS speculative batch; <= 0: automatic */
+} mc_estimate_params;
+
+typedef struct {
+    int64_t samples;    /* samples that entered the estimate */
+    int64_t switches;   /* AGS: treelet switches */
+    int64_t covered;    /* AGS: graphlets covered */
+    int64_t batches;    /* device batches launched */
+    int64_t discarded;  /* AGS: speculative samples drawn and not used */
+} mc_estimate_stats;
+
+/* est: host double[N_h], the estimated number of induced copies of each
+ * h-node graphlet in G; hits: host uint64[N_h], samples per graphlet;
+ * stats: host, may be NULL.  N_h = mc_num_classes(h).  Synchronises. */
+mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *params, double *est,
+                             uint64_t *hits, mc_estimate_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Catalogue (computed on the current device on first use, then cached)      */
+/* ------------------------------------------------------------------------ */
+int mc_num_shapes(int h);          /* rooted treelet shapes on h nodes */
+int mc_num_unrooted(int h);        /* unrooted treelet shapes on h nodes */
+int mc_num_classes(int h);         /* connected h-node graphs; -1 on error */
+/* Rooted shapes of size h in id order: s_T as an integer of 2(h-1) bits
+ * (DFS from the root, 1 = away from the root, children in decreasing
+ * lexicographic order, Section 3.2.1), its unrooted shape id, beta_T and the
+ * ids of T' and T'' (-1 for h = 1).  Host arrays of mc_num_shapes(h). */
+mc_status mc_shape_info(int h, uint32_t *code, int32_t *unrooted, int32_t *beta, int32_t *left,
+                        int32_t *right);
+/* Canonical adjacency words of the connected h-node graphs, ascending (host
+ * uint32[mc_num_classes(h)]).  Word of a labelled graph: pairs (i, j), i < j,
+ * in lexicographic order, the first pair in the most significant of the
+ * C(h,2) bits; canonical word: the smallest over all relabelings. */
+mc_status mc_class_codes(int h, uint32_t *codes);
+/* sigma_i (spanning trees of class i) and sigma_ij (those isomorphic to
+ * unrooted shape j), host int64[N_h] and int64[N_h * mc_num_unrooted(h)]. */
+mc_status mc_sigma(int h, int64_t *sigma_i, int64_t *sigma_ij);
+
+/* ------------------------------------------------------------------------ */
+/* Tracing                                                                   */
+/* ------------------------------------------------------------------------ */
+/* When enabled, every kernel the library launches is bracketed by CUDA
+ * events recorded on its own stream.  mc_profile_read synchronises those
+ * events and reports, per kernel name, the summed device time (ms) and the
+ * number of launches: names are written NUL-separated into `names`, at most
+ * `max` kernels, their number into *count.  mc_launch_count is the number of
+ * kernels launched since the library was loaded, whether or not profiling
+ * is on.  Profiling state is process-wide and not thread-safe. */
+mc_status mc_profile_enable(int on);
+mc_status mc_profile_reset(void);
+mc_status mc_profile_read(char *names, size_t names_bytes, double *ms, int64_t *launches, int max,
+                          int *count);
+int64_t mc_launch_count(void);
+
+const char *mc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOTIF_H */

@@ -67,6 +67,7 @@ void oc_color(int64_t n, int k, uint64_t seed, uint8_t *colors)
  * >= W, accepted when < W, else attempt + 1. */
 static u128 draw_below(uint64_t seed, uint64_t index, uint32_t step, u128 W)
 {
+    if (W == 0) abort();   /* a weight of zero here is a broken table */
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     int bits = 0;
     u128 wm1 = W - 1;

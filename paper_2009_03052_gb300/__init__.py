@@ -1,0 +1,381 @@
+"""Python binding of libmotif, the GB300 colour-coding motif library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library declared by include/motif.h.  PyTorch supplies device memory (the
+caching allocator, through the library's allocator callback) and streams.
+There is no CPU fallback: without the compiled library, or without a CUDA
+device, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build_ext
+
+LIB_PATH = build_ext.LIB
+_lock = threading.Lock()
+_lib = None
+
+MC_OK, MC_E_INVALID, MC_E_NOMEM, MC_E_OVERFLOW, MC_E_CUDA, MC_E_TIMEOUT, MC_E_UNSUPPORTED, \
+    MC_E_INTERNAL = range(8)
+MC_GRAPH_DEVICE_PTRS = 1
+MC_GRAPH_TRUSTED = 2
+MC_EST_UNIFORM = 0
+MC_EST_AGS = 1
+
+EXPORTED = [
+    "mc_load_graph", "mc_free_graph", "mc_graph_info", "mc_color", "mc_build_tables",
+    "mc_free_tables", "mc_total", "mc_table_layout", "mc_read_table", "mc_sample",
+    "mc_estimate_counts", "mc_num_shapes", "mc_num_unrooted", "mc_num_classes", "mc_shape_info",
+    "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
+    "mc_profile_read", "mc_launch_count",
+]
+
+
+class MotifError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libmotif status {status}: {msg}")
+        self.status = status
+
+
+class MotifOverflow(MotifError):
+    pass
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)),
+                ("ctx", C.c_void_p)]
+
+
+class EstimateParams(C.Structure):
+    _fields_ = [("mode", C.c_int), ("h", C.c_int), ("seed", C.c_uint64),
+                ("first_index", C.c_uint64), ("samples", C.c_int64), ("cbar", C.c_int64),
+                ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64)]
+
+
+class EstimateStats(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("switches", C.c_int64), ("covered", C.c_int64),
+                ("batches", C.c_int64), ("discarded", C.c_int64)]
+
+
+def load(path: str | None = None):
+    """Load libmotif; raises if it has not been built (see build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libmotif is not built ({p} missing); run "
+                               "paper_2009_03052_gb300.build()")
+        lib = C.CDLL(p)
+        P, i64, u64, i32 = C.c_void_p, C.c_int64, C.c_uint64, C.c_int32
+        lib.mc_load_graph.argtypes = [i64, i64, P, P, C.c_uint32, P, P, C.POINTER(P)]
+        lib.mc_free_graph.argtypes = [P]
+        lib.mc_free_graph.restype = None
+        lib.mc_graph_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        lib.mc_color.argtypes = [P, C.c_int, u64, P, P]
+        lib.mc_build_tables.argtypes = [P, P, C.c_int, C.c_int, C.c_uint32, P, P, C.POINTER(P)]
+        lib.mc_free_tables.argtypes = [P]
+        lib.mc_free_tables.restype = None
+        lib.mc_total.argtypes = [P, C.c_int, i32, P, P, P]
+        lib.mc_table_layout.argtypes = [P, C.c_int, C.c_int, C.POINTER(i64), C.POINTER(C.c_int)]
+        lib.mc_read_table.argtypes = [P, C.c_int, C.c_int, P, C.c_size_t, C.c_int, P]
+        lib.mc_sample.argtypes = [P, C.c_int, i32, u64, u64, i64, P, P, P, P, P]
+        lib.mc_estimate_counts.argtypes = [P, C.POINTER(EstimateParams), P, P,
+                                           C.POINTER(EstimateStats), P]
+        for f in ("mc_num_shapes", "mc_num_unrooted", "mc_num_classes"):
+            getattr(lib, f).argtypes = [C.c_int]
+        lib.mc_shape_info.argtypes = [C.c_int, P, P, P, P, P]
+        lib.mc_class_codes.argtypes = [C.c_int, P]
+        lib.mc_sigma.argtypes = [C.c_int, P, P]
+        lib.mc_last_error.restype = C.c_char_p
+        lib.mc_profile_enable.argtypes = [C.c_int]
+        lib.mc_profile_read.argtypes = [P, C.c_size_t, P, P, C.c_int, C.POINTER(C.c_int)]
+        lib.mc_launch_count.restype = C.c_int64
+        _lib = lib
+        return lib
+
+
+def build(force: bool = False) -> str:
+    """Compile libmotif for sm_103a in-tree."""
+    return build_ext.build(force=force)
+
+
+def _check(st: int):
+    if st != MC_OK:
+        msg = (load().mc_last_error() or b"").decode()
+        if st == MC_E_OVERFLOW:
+            raise MotifOverflow(st, msg)
+        raise MotifError(st, msg)
+
+
+# ---------------------------------------------------------------------------
+# torch plumbing: device memory and streams
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libmotif needs a CUDA device")
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class TorchAllocator:
+    """Allocator callbacks backed by torch's caching allocator."""
+
+    def __init__(self):
+        torch = _torch()
+        self.device = torch.cuda.current_device()
+        dev = self.device
+
+        @C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+        def _alloc(nbytes, ctx, stream):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+            except Exception:
+                return None
+
+        @C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+        def _free(ptr, nbytes, ctx, stream):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._keep = (_alloc, _free)
+        self.struct = Allocator(_alloc, _free, None)
+
+
+_allocator = None
+
+
+def torch_allocator() -> TorchAllocator:
+    global _allocator
+    if _allocator is None:
+        _allocator = TorchAllocator()
+    return _allocator
+
+
+def _ptr(x) -> int:
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x.ctypes.data)
+
+
+def _u128(a) -> int:
+    return int(a[0]) | (int(a[1]) << 64)
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """mc_load_graph: a CSR graph copied to the device."""
+
+    def __init__(self, row_ptr, col, trusted: bool = False, stream=None):
+        lib = load()
+        torch = _torch()
+        on_dev = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
+        if not on_dev:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.uint32)
+        n = int(row_ptr.shape[0]) - 1
+        nnz = int(col.shape[0])
+        flags = (MC_GRAPH_DEVICE_PTRS if on_dev else 0) | (MC_GRAPH_TRUSTED if trusted else 0)
+        self._alloc = torch_allocator()
+        h = C.c_void_p()
+        _check(lib.mc_load_graph(n, nnz, _ptr(row_ptr), _ptr(col) if nnz else None, flags,
+                                 C.byref(self._alloc.struct), _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+        self.n, self.nnz = n, nnz
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_csr(cls, g, **kw) -> "Graph":
+        return cls(g.row_ptr, g.col, **kw)
+
+    def info(self) -> tuple[int, int, int]:
+        n, nnz, md = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().mc_graph_info(self.handle, C.byref(n), C.byref(nnz), C.byref(md)))
+        return n.value, nnz.value, md.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().mc_free_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def color(graph: Graph, k: int, seed: int, out=None, stream=None):
+    """mc_color: counter-based uniform colouring, a device uint8 tensor."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(max(graph.n, 1), dtype=torch.uint8, device="cuda")
+    _check(load().mc_color(graph.handle, k, seed, _ptr(out), _stream_ptr(stream)))
+    return out[: graph.n]
+
+
+class Tables:
+    """mc_build_tables: the exact colourful treelet count tables."""
+
+    def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None):
+        torch = _torch()
+        if not (hasattr(colors, "is_cuda") and colors.is_cuda):
+            colors = torch.as_tensor(np.ascontiguousarray(colors, dtype=np.uint8)).cuda()
+        self.graph, self.k, self.bits = graph, k, count_bits
+        self._alloc = torch_allocator()
+        h = C.c_void_p()
+        _check(load().mc_build_tables(graph.handle, _ptr(colors) if graph.n else None, k,
+                                      count_bits, 0, C.byref(self._alloc.struct),
+                                      _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().mc_free_tables(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def total(self, h: int, unrooted: int = -1, stream=None) -> tuple[int, int]:
+        """mc_total: (rooted total, number of colourful h-treelet copies)."""
+        r = np.zeros(2, np.uint64)
+        u = np.zeros(2, np.uint64)
+        _check(load().mc_total(self.handle, h, unrooted, _ptr(r), _ptr(u), _stream_ptr(stream)))
+        return _u128(r), _u128(u)
+
+    def layout(self, h: int, which: int = 0) -> tuple[int, int]:
+        w, b = C.c_int64(), C.c_int()
+        _check(load().mc_table_layout(self.handle, h, which, C.byref(w), C.byref(b)))
+        return w.value, b.value
+
+    def read(self, h: int, which: int = 0, stream=None) -> np.ndarray:
+        """mc_read_table into host memory: uint64 array [n, W, words] (words
+        = 1 for 64-bit counts, 2 for 128-bit ones, low word first)."""
+        W, b = self.layout(h, which)
+        words = b // 8
+        out = np.zeros(max(self.graph.n * W * words, 1), np.uint64)
+        _check(load().mc_read_table(self.handle, h, which, _ptr(out), out.nbytes, 0,
+                                    _stream_ptr(stream)))
+        return out[: self.graph.n * W * words].reshape(self.graph.n, W, words)
+
+    def sample(self, h: int, seed: int, first_index: int, count: int, unrooted: int = -1,
+               nodes=True, roots=True, shapes=True, classes=True, stream=None):
+        """mc_sample: device tensors (nodes [count, h], roots, shapes, classes)."""
+        torch = _torch()
+        dev = "cuda"
+        t_nodes = torch.empty((max(count, 1), h), dtype=torch.int32, device=dev) if nodes else None
+        t_roots = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if roots else None
+        t_shapes = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if shapes else None
+        t_cls = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if classes else None
+        p = lambda t: _ptr(t) if t is not None else None
+        _check(load().mc_sample(self.handle, h, unrooted, seed, first_index, count, p(t_nodes),
+                                p(t_roots), p(t_shapes), p(t_cls), _stream_ptr(stream)))
+        cut = lambda t: t[:count] if t is not None else None
+        return cut(t_nodes), cut(t_roots), cut(t_shapes), cut(t_cls)
+
+    def estimate(self, h: int, seed: int, samples: int, mode: int = MC_EST_UNIFORM,
+                 first_index: int = 0, cbar: int = 0, eps: float = 0.0, delta: float = 0.0,
+                 batch: int = 0, stream=None):
+        """mc_estimate_counts: (estimates, hits, stats dict)."""
+        ncls = num_classes(h)
+        est = np.zeros(ncls, np.float64)
+        hits = np.zeros(ncls, np.uint64)
+        prm = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch)
+        st = EstimateStats()
+        _check(load().mc_estimate_counts(self.handle, C.byref(prm), _ptr(est), _ptr(hits),
+                                         C.byref(st), _stream_ptr(stream)))
+        return est, hits, {"samples": st.samples, "switches": st.switches,
+                           "covered": st.covered, "batches": st.batches,
+                           "discarded": st.discarded}
+
+
+# ---------------------------------------------------------------------------
+# catalogue
+# ---------------------------------------------------------------------------
+
+def num_shapes(h: int) -> int:
+    return int(load().mc_num_shapes(h))
+
+
+def num_unrooted(h: int) -> int:
+    return int(load().mc_num_unrooted(h))
+
+
+def num_classes(h: int) -> int:
+    n = int(load().mc_num_classes(h))
+    if n < 0:
+        _check(MC_E_INTERNAL)
+    return n
+
+
+def shape_info(h: int) -> dict:
+    r = num_shapes(h)
+    code = np.zeros(r, np.uint32)
+    arrs = [np.zeros(r, np.int32) for _ in range(4)]
+    _check(load().mc_shape_info(h, _ptr(code), *[_ptr(a) for a in arrs]))
+    return {"code": code, "unrooted": arrs[0], "beta": arrs[1], "left": arrs[2],
+            "right": arrs[3]}
+
+
+def class_codes(h: int) -> np.ndarray:
+    out = np.zeros(num_classes(h), np.uint32)
+    _check(load().mc_class_codes(h, _ptr(out)))
+    return out
+
+
+def sigma(h: int) -> tuple[np.ndarray, np.ndarray]:
+    nc, nu = num_classes(h), num_unrooted(h)
+    si = np.zeros(nc, np.int64)
+    sij = np.zeros(nc * nu, np.int64)
+    _check(load().mc_sigma(h, _ptr(si), _ptr(sij)))
+    return si, sij.reshape(nc, nu)
+
+
+# ---------------------------------------------------------------------------
+# tracing
+# ---------------------------------------------------------------------------
+
+def profile_enable(on: bool = True):
+    _check(load().mc_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().mc_profile_reset())
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} of the library's own kernels."""
+    maxk = 256
+    names = C.create_string_buffer(maxk * 32)
+    ms = np.zeros(maxk, np.float64)
+    launches = np.zeros(maxk, np.int64)
+    cnt = C.c_int()
+    _check(load().mc_profile_read(names, len(names), _ptr(ms), _ptr(launches), maxk,
+                                  C.byref(cnt)))
+    out = {}
+    parts = names.raw.split(b"\0")
+    for i in range(cnt.value):
+        out[parts[i].decode()] = (float(ms[i]), int(launches[i]))
+    return out
+
+
+def launch_count() -> int:
+    return int(load().mc_launch_count())

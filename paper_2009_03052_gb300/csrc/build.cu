@@ -1,0 +1,639 @@
+// build.cu -- the colourful treelet count tables (Section 2.1, Eq. 1).
+//
+// Per level h the dynamic program runs as two kernels:
+//   gather: S_h(v)[T'', C''] = sum_{u ~ v} c_h(u)[T'', C'']      (HBM bound)
+//   merge : c_h(v)[T, C] = (1/beta_T) sum_{C' + C'' = C} c_{|T'|}(v)[T', C'] S_{|T''|}(v)[T'', C'']
+// with T -> (T', T'') the canonical decomposition (T'' the subtree of the
+// root's first child).  Rows are colour-relative: at node v only colour sets
+// containing c_v (for c) or avoiding it (for S) are stored, indexed by the
+// colex rank of the set with c_v deleted from the palette, so the merge's
+// index structure is the same at every node and the gather reads only live
+// entries of the neighbour's row.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace mc {
+
+enum : int { ERR_OVERFLOW = 1, ERR_INEXACT = 2, ERR_COLOUR = 4, ERR_SEARCH = 8 };
+
+// ---------------------------------------------------------------------------
+// level 1: S_1(v)[{a}] = number of neighbours of colour a != c_v
+// (c(single node, {c_u}, u) = 1).  One warp per node; one ballot per colour.
+// ---------------------------------------------------------------------------
+template <typename CT>
+__global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict__ row_ptr,
+                                                      const uint32_t *__restrict__ col,
+                                                      const uint8_t *__restrict__ colors, int64_t n,
+                                                      int k, CT *__restrict__ S1)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const int cv = colors[v];
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        uint32_t cnt = 0;  // lane a (< k-1) counts relative colour a
+        for (int64_t b = e0; b < e1; b += 32) {
+            const int64_t e = b + lane;
+            const int cu = e < e1 ? (int)colors[col[e]] : -1;
+            for (int a = 0; a < k - 1; ++a) {
+                const int abs_a = a < cv ? a : a + 1;
+                const unsigned m = __ballot_sync(0xffffffffu, cu == abs_a);
+                if (lane == a) cnt += __popc(m);
+            }
+        }
+        if (lane < k - 1) S1[v * (k - 1) + lane] = (CT)cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// level h >= 2 neighbour sums.  One warp per task; a task is a node (all its
+// neighbours) or a chunk of HUB_CHUNK neighbours of a hub, whose partial row
+// goes to `partial`.  The warp splits into 32/G groups of G lanes; a group
+// takes one neighbour at a time, its lanes the S entries (lane j owns
+// entries j, j+G, ...).  The colour-relative index map for (c_v, c_u) lives
+// in shared memory.
+// ---------------------------------------------------------------------------
+struct GatherArgs {
+    const int64_t *row_ptr;
+    const uint32_t *col;
+    const uint8_t *colors;
+    const void *src;   // c_h, n x Wc
+    void *dst;         // S_h, n x Ws
+    void *partial;     // n_chunks x Ws
+    const uint32_t *chunk_node;
+    const int64_t *chunk_e0, *chunk_e1;
+    const int16_t *gmap;
+    int64_t n, n_chunks;
+    int k, Bc, Bs, Wc, Ws;
+    int *err;
+};
+
+template <typename CT, int G, int MAXE>
+__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a)
+{
+    extern __shared__ int16_t s_map[];
+    const int mapn = a.k * a.k * a.Bs;
+    for (int i = threadIdx.x; i < mapn; i += blockDim.x) s_map[i] = a.gmap[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, j = lane % G;
+    constexpr int NG = 32 / G;
+    int rowoff[MAXE], rho[MAXE];
+    bool own[MAXE];
+#pragma unroll
+    for (int i = 0; i < MAXE; ++i) {
+        const int e = j + i * G;
+        own[i] = e < a.Ws;
+        const int s = e / a.Bs;
+        rho[i] = own[i] ? e - s * a.Bs : 0;
+        rowoff[i] = own[i] ? s * a.Bc : 0;
+    }
+    const CT *__restrict__ src = (const CT *)a.src;
+    const int64_t ntasks = a.n_chunks + a.n;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool ovf = false;
+    for (int64_t t = warp; t < ntasks; t += nwarps) {
+        int64_t v, e0, e1;
+        CT *out;
+        if (t < a.n_chunks) {
+            v = a.chunk_node[t];
+            e0 = a.chunk_e0[t];
+            e1 = a.chunk_e1[t];
+            out = (CT *)a.partial + t * a.Ws;
+        } else {
+            v = t - a.n_chunks;
+            e0 = a.row_ptr[v];
+            e1 = a.row_ptr[v + 1];
+            if (e1 - e0 > HUB_CHUNK) continue;  // done by its chunks
+            out = (CT *)a.dst + v * a.Ws;
+        }
+        const int cv = a.colors[v];
+        CT acc[MAXE];
+#pragma unroll
+        for (int i = 0; i < MAXE; ++i) acc[i] = 0;
+        for (int64_t e = e0 + grp; e < e1; e += NG) {
+            const uint32_t u = a.col[e];
+            const int cu = a.colors[u];
+            if (cu == cv) continue;  // every set holding c_u also holds c_v
+            const CT *row = src + (int64_t)u * a.Wc;
+            const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
+#pragma unroll
+            for (int i = 0; i < MAXE; ++i) {
+                if (own[i]) {
+                    const int sidx = gm[rho[i]];
+                    if (sidx >= 0) ovf |= add_ovf(acc[i], row[rowoff[i] + sidx]);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = G; d < 32; d <<= 1)
+#pragma unroll
+            for (int i = 0; i < MAXE; ++i) {
+                const CT o = shfl_xor(acc[i], d);
+                ovf |= add_ovf(acc[i], o);
+            }
+        if (grp == 0) {
+#pragma unroll
+            for (int i = 0; i < MAXE; ++i)
+                if (own[i]) out[j + i * G] = acc[i];
+        }
+    }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+}
+
+// Sum the chunk partials of each hub into its S row.
+template <typename CT>
+__global__ void hub_reduce_kernel(const CT *__restrict__ partial, CT *__restrict__ dst,
+                                  const uint32_t *__restrict__ hub_node,
+                                  const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int Ws,
+                                  int *err)
+{
+    bool ovf = false;
+    const int64_t total = n_hubs * Ws;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t hub = i / Ws;
+        const int e = (int)(i - hub * Ws);
+        CT s = 0;
+        for (int64_t c = hub_chunk0[hub]; c < hub_chunk0[hub + 1]; ++c) ovf |= add_ovf(s, partial[c * Ws + e]);
+        dst[(int64_t)hub_node[hub] * Ws + e] = s;
+    }
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
+// ---------------------------------------------------------------------------
+// merge of level h: one thread per (node, output entry).  Output o of level
+// h carries (|T'|, |T''|, beta, #terms) and a list of (index into the
+// c_{|T'|} row, index into the S_{|T''|} row) pairs, one per split of the
+// colour set; c_1 is the constant 1.
+// ---------------------------------------------------------------------------
+struct MergeArgs {
+    const void *c[MAXK + 1];
+    const void *S[MAXK + 1];
+    int Wc[MAXK + 1], Ws[MAXK + 1];
+    ExactDiv div[MAXK + 1];
+    const int32_t *info, *off;
+    const uint32_t *terms;
+    void *out;
+    int64_t n;
+    int W;
+    int *err;
+};
+
+template <typename CT>
+__global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ MergeArgs a)
+{
+    bool ovf = false, inexact = false;
+    const int64_t total = a.n * a.W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / a.W;
+        const int o = (int)(t - v * a.W);
+        const int info = a.info[o];
+        const int h1 = info & 15, h2 = (info >> 4) & 15, beta = (info >> 8) & 255, nt = info >> 16;
+        const uint32_t *term = a.terms + a.off[o];
+        const CT *B = (const CT *)a.S[h2] + v * a.Ws[h2];
+        CT sum = 0;
+        if (h1 == 1) {
+            for (int i = 0; i < nt; ++i) ovf |= add_ovf(sum, B[term[i] >> 16]);
+        } else {
+            const CT *A = (const CT *)a.c[h1] + v * a.Wc[h1];
+            for (int i = 0; i < nt; ++i) {
+                const uint32_t tm = term[i];
+                CT p;
+                ovf |= mul_ovf(A[tm & 0xffffu], B[tm >> 16], p);
+                ovf |= add_ovf(sum, p);
+            }
+        }
+        CT q;
+        if (!exact_div(sum, a.div[beta], q)) inexact = true;
+        ((CT *)a.out)[t] = q;
+    }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (inexact) atomicOr(a.err, ERR_INEXACT);
+}
+
+// ---------------------------------------------------------------------------
+// per-node totals of a level over a set of shapes, and an inclusive u128
+// prefix over the nodes (the cumulative counts of Section 3.2.1, taken over
+// nodes for the root draw).
+// ---------------------------------------------------------------------------
+template <typename CT>
+__global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ c, int64_t n, int W, int Bc,
+                                                         uint64_t allow0, uint64_t allow1,
+                                                         u128 *__restrict__ tot, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool ovf = false;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        u128 s = 0;
+        for (int e = lane; e < W; e += 32) {
+            const int sh = e / Bc;
+            const bool ok = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
+            if (ok) ovf |= add_ovf(s, widen(c[v * W + e]));
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            const u128 o = shfl_xor(s, d);
+            ovf |= add_ovf(s, o);
+        }
+        if (lane == 0) tot[v] = s;
+    }
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
+constexpr int SCAN_THREADS = 512, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ u128 block_exclusive_scan(u128 x, u128 *smem, u128 &block_total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u128 inc = warp_inclusive_scan(x);
+    if (lane == 31) smem[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        u128 y = lane < nw ? smem[lane] : 0;
+        y = warp_inclusive_scan(y);
+        if (lane < nw) smem[lane] = y;
+    }
+    __syncthreads();
+    const u128 before = w > 0 ? smem[w - 1] : 0;
+    block_total = smem[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + inc - x;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_kernel(const u128 *__restrict__ x, int64_t n,
+                                                                  u128 *__restrict__ tile_sum, int *err)
+{
+    __shared__ u128 smem[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    u128 s = 0;
+    bool ovf = false;
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < n) ovf |= add_ovf(s, x[base + i]);
+    u128 tot;
+    const u128 ex = block_exclusive_scan(s, smem, tot);
+    // the block total is exact iff no prefix wrapped
+    if (ex + s < ex) ovf = true;
+    if (threadIdx.x == blockDim.x - 1) tile_sum[blockIdx.x] = tot;
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(1024) scan_tile_sums_kernel(u128 *tile_sum, int64_t ntiles, int *err)
+{
+    __shared__ u128 smem[32];
+    u128 carry = 0;
+    bool ovf = false;
+    for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        const u128 x = i < ntiles ? tile_sum[i] : 0;
+        u128 tot;
+        const u128 ex = block_exclusive_scan(x, smem, tot);
+        const u128 before = carry + ex;
+        if (before < carry || before + x < before) ovf = true;
+        if (i < ntiles) tile_sum[i] = before;  // exclusive
+        const u128 nc = carry + tot;
+        if (nc < carry) ovf = true;
+        carry = nc;
+    }
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_apply_kernel(u128 *__restrict__ x, int64_t n,
+                                                                  const u128 *__restrict__ tile_ex)
+{
+    __shared__ u128 smem[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    u128 v[SCAN_ITEMS];
+    u128 s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? x[base + i] : 0;
+        s += v[i];
+    }
+    u128 tot;
+    u128 run = block_exclusive_scan(s, smem, tot) + tile_ex[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        run += v[i];
+        if (base + i < n) x[base + i] = run;
+    }
+}
+
+__global__ void check_colours_kernel(const uint8_t *colors, int64_t n, int k, int *err)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (colors[v] >= k) atomicOr(err, ERR_COLOUR);
+}
+
+__global__ void fill_ones_kernel(void *dst, int64_t n, int bytes)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (bytes == 8) ((uint64_t *)dst)[i] = 1;
+        else ((u128 *)dst)[i] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    u128 *ts = scratch.get<u128>((size_t)ntiles);
+    MC_LAUNCH("scan_tiles", s, scan_tiles_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(x, n, ts, err));
+    MC_LAUNCH("scan_tile_sums", s, scan_tile_sums_kernel<<<1, 1024, 0, s>>>(ts, ntiles, err));
+    MC_LAUNCH("scan_apply", s, scan_apply_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(x, n, ts));
+}
+
+ExactDiv make_div(int beta)
+{
+    ExactDiv d{};
+    int t = 0;
+    while (!((beta >> t) & 1)) ++t;
+    const uint64_t odd = (uint64_t)(beta >> t);
+    // Newton iteration for the inverse of an odd number modulo 2^64 / 2^128
+    uint64_t inv = odd;  // correct to 3 bits
+    for (int i = 0; i < 6; ++i) inv *= 2 - odd * inv;
+    u128 inv2 = inv;
+    for (int i = 0; i < 2; ++i) inv2 *= (u128)2 - (u128)odd * inv2;
+    d.shift = t;
+    d.inv64 = inv;
+    d.inv128 = inv2;
+    d.qmax64 = ~0ull / odd;
+    d.qmax128 = (~(u128)0) / (u128)odd;
+    return d;
+}
+
+template <typename CT> size_t bytes_of() { return sizeof(CT); }
+
+void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
+                       cudaStream_t s)
+{
+    const int64_t n = t->g->n;
+    if (n == 0) return;
+    const int W = t->geo.Wc[h], Bc = t->geo.Bc[h];
+    const int grid = grid_for(n * 32, 256);
+    if (t->bits == 64)
+        MC_LAUNCH("row_totals", s, row_totals_kernel<uint64_t><<<grid, 256, 0, s>>>((const uint64_t *)t->c[h], n, W, Bc, allow0, allow1, tot, err));
+    else
+        MC_LAUNCH("row_totals", s, row_totals_kernel<u128><<<grid, 256, 0, s>>>((const u128 *)t->c[h], n, W, Bc, allow0, allow1, tot, err));
+}
+
+static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gather_h2", "gather_h3",
+                                                  "gather_h4", "gather_h5", "gather_h6", "gather_h7",
+                                                  "gather_h8"};
+static const char *const kMergeName[MAXK + 1] = {"merge_h0", "merge_h1", "merge_h2", "merge_h3", "merge_h4",
+                                                 "merge_h5", "merge_h6", "merge_h7", "merge_h8"};
+
+template <typename CT> static void launch_gather(const GatherArgs &ga, int G, int h, cudaStream_t s)
+{
+    const char *nm = kGatherName[h];
+    const int64_t ntasks = ga.n_chunks + ga.n;
+    const int grid = grid_for(ntasks * 32, 256);
+    const size_t smem = (size_t)ga.k * ga.k * ga.Bs * sizeof(int16_t);
+    switch (G) {
+    case 1: MC_LAUNCH(nm, s, gather_kernel<CT, 1, 1><<<grid, 256, smem, s>>>(ga)); break;
+    case 2: MC_LAUNCH(nm, s, gather_kernel<CT, 2, 1><<<grid, 256, smem, s>>>(ga)); break;
+    case 4: MC_LAUNCH(nm, s, gather_kernel<CT, 4, 1><<<grid, 256, smem, s>>>(ga)); break;
+    case 8: MC_LAUNCH(nm, s, gather_kernel<CT, 8, 1><<<grid, 256, smem, s>>>(ga)); break;
+    case 16: MC_LAUNCH(nm, s, gather_kernel<CT, 16, 1><<<grid, 256, smem, s>>>(ga)); break;
+    default: MC_LAUNCH(nm, s, gather_kernel<CT, 32, 6><<<grid, 256, smem, s>>>(ga)); break;
+    }
+}
+
+template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &scratch, cudaStream_t s)
+{
+    const mc_graph *g = t->g;
+    const Geometry &G = t->geo;
+    const int k = t->k;
+    const int64_t n = g->n;
+    if (n == 0) return;
+    // level 1 neighbour sums
+    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, g->col, t->colors, n, k, (CT *)t->S[1]));
+    int maxWs = 0;
+    for (int h = 2; h <= k - 1; ++h) maxWs = std::max(maxWs, G.Ws[h]);
+    CT *partial = g->n_chunks && maxWs ? scratch.get<CT>((size_t)g->n_chunks * maxWs) : nullptr;
+
+    MergeArgs ma{};
+    for (int h = 1; h <= k; ++h) {
+        ma.c[h] = t->c[h];
+        ma.S[h] = t->S[h];
+        ma.Wc[h] = G.Wc[h];
+        ma.Ws[h] = G.Ws[h];
+        if (h <= MAXK) ma.div[h] = make_div(h);
+    }
+    ma.n = n;
+    ma.err = err;
+    for (int h = 2; h <= k; ++h) {
+        ma.info = t->m_info[h];
+        ma.off = t->m_off[h];
+        ma.terms = t->m_terms[h];
+        ma.out = t->c[h];
+        ma.W = G.Wc[h];
+        MC_LAUNCH(kMergeName[h], s, merge_kernel<CT><<<grid_for(n * G.Wc[h], 256), 256, 0, s>>>(ma));
+        if (h <= k - 1) {
+            GatherArgs ga{};
+            ga.row_ptr = g->row_ptr;
+            ga.col = g->col;
+            ga.colors = t->colors;
+            ga.src = t->c[h];
+            ga.dst = t->S[h];
+            ga.partial = partial;
+            ga.chunk_node = g->chunk_node;
+            ga.chunk_e0 = g->chunk_e0;
+            ga.chunk_e1 = g->chunk_e1;
+            ga.gmap = t->g_map[h];
+            ga.n = n;
+            ga.n_chunks = g->n_chunks;
+            ga.k = k;
+            ga.Bc = G.Bc[h];
+            ga.Bs = G.Bs[h];
+            ga.Wc = G.Wc[h];
+            ga.Ws = G.Ws[h];
+            ga.err = err;
+            int grp = 1;
+            while (grp < G.Ws[h] && grp < 32) grp <<= 1;
+            launch_gather<CT>(ga, grp, h, s);
+            if (g->n_hubs) {
+                MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
+                    partial, (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
+            }
+        }
+    }
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
+                                     uint32_t flags, const mc_allocator *alloc, void *stream,
+                                     mc_tables **out)
+{
+    if (out) *out = nullptr;
+    mc_tables *t = nullptr;
+    mc_status st = guarded([&] {
+        MC_REQUIRE(out && g, "graph or out is NULL");
+        MC_REQUIRE(colors || g->n == 0, "colors is NULL");
+        if (k < 2 || k > MAXK) throw Error(MC_E_UNSUPPORTED, "k must be in 2..8");
+        MC_REQUIRE(count_bits == 64 || count_bits == 128, "count_bits must be 64 or 128");
+        MC_REQUIRE(flags == 0, "unknown flags");
+        cudaStream_t s = (cudaStream_t)stream;
+        t = new mc_tables();
+        t->g = g;
+        t->k = k;
+        t->bits = count_bits;
+        t->geo = make_geometry(k);
+        t->arena.stream = s;
+        if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
+        Arena scratch;
+        scratch.alloc = t->arena.alloc;
+        scratch.stream = s;
+        const int64_t n = g->n;
+        const Geometry &G = t->geo;
+        const size_t cb = count_bits / 8;
+        int *err = scratch.get<int>(4);
+        MC_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+        t->colors = t->arena.get<uint8_t>((size_t)n);
+        if (n) {
+            MC_CUDA(cudaMemcpyAsync(t->colors, colors, (size_t)n, cudaMemcpyDefault, s));
+            MC_LAUNCH("check_colours", s, check_colours_kernel<<<grid_for(n, 256), 256, 0, s>>>(t->colors, n, k, err));
+        }
+        // programs
+        const Programs &P = programs(k);
+        for (int h = 2; h <= k; ++h) {
+            const MergeLevel &M = P.merge[h];
+            t->m_info[h] = t->arena.get<int32_t>(M.info.size());
+            t->m_off[h] = t->arena.get<int32_t>(M.offset.size());
+            t->m_terms[h] = t->arena.get<uint32_t>(M.terms.size());
+            MC_CUDA(cudaMemcpyAsync(t->m_info[h], M.info.data(), M.info.size() * 4, cudaMemcpyHostToDevice, s));
+            MC_CUDA(cudaMemcpyAsync(t->m_off[h], M.offset.data(), M.offset.size() * 4, cudaMemcpyHostToDevice, s));
+            MC_CUDA(cudaMemcpyAsync(t->m_terms[h], M.terms.data(), M.terms.size() * 4, cudaMemcpyHostToDevice, s));
+        }
+        for (int h = 1; h <= k - 1; ++h) {
+            const GatherLevel &L = P.gather[h];
+            t->g_map[h] = t->arena.get<int16_t>(L.map.size());
+            MC_CUDA(cudaMemcpyAsync(t->g_map[h], L.map.data(), L.map.size() * 2, cudaMemcpyHostToDevice, s));
+        }
+        // tables
+        for (int h = 2; h <= k; ++h) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
+        for (int h = 1; h <= k - 1; ++h) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
+        for (int h = 2; h <= k; ++h) t->prefix[h] = t->arena.get<u128>((size_t)n);
+        if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
+        else build_levels<u128>(t, err, scratch, s);
+        // node prefixes of the level totals, for the root draw
+        for (int h = 2; h <= k; ++h) {
+            launch_row_totals(t, h, ~0ull, ~0ull, t->prefix[h], err, s);
+            inclusive_scan_u128(t->prefix[h], n, err, scratch, s);
+        }
+        int herr = 0;
+        MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        for (int h = 2; h <= k; ++h)
+            if (n) MC_CUDA(cudaMemcpyAsync(&t->R[h], t->prefix[h] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (herr & ERR_COLOUR) throw Error(MC_E_INVALID, "a colour is >= k");
+        if (herr & ERR_OVERFLOW)
+            throw Error(MC_E_OVERFLOW, "a count does not fit in " + std::to_string(count_bits) + " bits");
+        if (herr & ERR_INEXACT) throw Error(MC_E_INTERNAL, "a merge numerator is not divisible by beta");
+    });
+    if (st != MC_OK) { delete t; return st; }
+    *out = t;
+    return MC_OK;
+}
+
+extern "C" void mc_free_tables(mc_tables *t) { delete t; }
+
+extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
+                              uint64_t unrooted_count[2], void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t && rooted && unrooted_count, "NULL argument");
+        MC_REQUIRE(h >= 1 && h <= t->k, "h must be in 1..k");
+        const ShapeCatalog &cat = shape_catalog();
+        MC_REQUIRE(unrooted_shape < cat.n_unrooted[h], "unrooted shape out of range");
+        u128 R = 0;
+        if (h == 1) {
+            R = (u128)t->g->n;
+            if (unrooted_shape > 0) R = 0;
+        } else if (unrooted_shape < 0) {
+            R = t->R[h];
+        } else if (t->g->n > 0) {
+            cudaStream_t s = (cudaStream_t)stream;
+            uint64_t a0 = 0, a1 = 0;
+            for (int i = 0; i < cat.r[h]; ++i)
+                if (cat.shapes[cat.gid(h, i)].unrooted == unrooted_shape) {
+                    if (i < 64) a0 |= 1ull << i; else a1 |= 1ull << (i - 64);
+                }
+            Arena scratch;
+            scratch.alloc = t->arena.alloc;
+            scratch.stream = s;
+            int *err = scratch.get<int>(1);
+            MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            u128 *tot = scratch.get<u128>((size_t)t->g->n);
+            launch_row_totals(t, h, a0, a1, tot, err, s);
+            inclusive_scan_u128(tot, t->g->n, err, scratch, s);
+            int herr = 0;
+            MC_CUDA(cudaMemcpyAsync(&R, tot + (t->g->n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            if (herr) throw Error(MC_E_OVERFLOW, "level total does not fit in 128 bits");
+        }
+        if (R % (u128)h != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
+        const u128 U = R / (u128)h;
+        rooted[0] = (uint64_t)R;
+        rooted[1] = (uint64_t)(R >> 64);
+        unrooted_count[0] = (uint64_t)U;
+        unrooted_count[1] = (uint64_t)(U >> 64);
+    });
+}
+
+extern "C" mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,
+                                     int *entry_bytes)
+{
+    return guarded([&] {
+        MC_REQUIRE(t, "tables is NULL");
+        MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
+        MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
+        if (row_entries) *row_entries = which ? t->geo.Ws[h] : t->geo.Wc[h];
+        if (entry_bytes) *entry_bytes = t->bits / 8;
+    });
+}
+
+extern "C" mc_status mc_read_table(const mc_tables *t, int h, int which, void *dst, size_t dst_bytes,
+                                   int dst_on_device, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t && dst, "NULL argument");
+        MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
+        MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
+        const int64_t W = which ? t->geo.Ws[h] : t->geo.Wc[h];
+        const size_t bytes = (size_t)t->g->n * W * (t->bits / 8);
+        MC_REQUIRE(dst_bytes >= bytes, "dst too small");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (bytes == 0) return;
+        if (which == 0 && h == 1) {
+            if (dst_on_device) {
+                MC_LAUNCH("fill_ones", s, fill_ones_kernel<<<grid_for(t->g->n, 256), 256, 0, s>>>(dst, t->g->n, t->bits / 8));
+            } else {
+                std::memset(dst, 0, bytes);
+                for (int64_t v = 0; v < t->g->n; ++v) ((uint8_t *)dst)[v * (t->bits / 8)] = 1;
+            }
+        } else {
+            const void *src = which ? t->S[h] : t->c[h];
+            MC_CUDA(cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        }
+        MC_CUDA(cudaStreamSynchronize(s));
+    });
+}

@@ -1,0 +1,140 @@
+// internal.h -- handle layouts, error plumbing and device memory helpers of
+// libmotif (host side).
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/motif.h"
+#include "catalog.h"
+#include "common.cuh"
+
+namespace mc {
+
+// An error carrying an mc_status; caught at the ABI boundary.
+struct Error : std::runtime_error {
+    mc_status status;
+    Error(mc_status s, const std::string &what) : std::runtime_error(what), status(s) {}
+};
+
+void set_last_error(const std::string &msg);
+
+#define MC_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            throw ::mc::Error(MC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define MC_REQUIRE(cond, msg)                                        \
+    do {                                                             \
+        if (!(cond)) throw ::mc::Error(MC_E_INVALID, msg);           \
+    } while (0)
+
+// Device memory through the caller's allocator (or cudaMalloc).
+struct Allocator {
+    mc_allocator a{};
+    bool custom = false;
+    void *alloc(size_t bytes, cudaStream_t s) const;
+    void release(void *p, size_t bytes, cudaStream_t s) const;
+};
+
+// A set of device buffers released together.
+struct Arena {
+    Allocator alloc;
+    cudaStream_t stream = nullptr;
+    std::vector<std::pair<void *, size_t>> blocks;
+    template <typename T> T *get(size_t count)
+    {
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 256;
+        void *p = alloc.alloc(bytes, stream);
+        if (!p) throw Error(MC_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        blocks.emplace_back(p, bytes);
+        return static_cast<T *>(p);
+    }
+    void release_all();
+    ~Arena() { release_all(); }
+};
+
+// Run f, turning exceptions into an mc_status and mc_last_error().
+template <typename F> mc_status guarded(F &&f)
+{
+    try {
+        f();
+        return MC_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return MC_E_NOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return MC_E_INTERNAL;
+    }
+}
+
+int grid_for(int64_t work, int block);
+int sm_count();
+
+// Kernel tracing: count every launch; when profiling is on, bracket it by
+// CUDA events on its stream, keyed by a kernel name.
+struct ProfSpan {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int id = -1;
+};
+ProfSpan prof_begin(const char *name, cudaStream_t s);
+void prof_end(ProfSpan &span, cudaStream_t s);
+
+#define MC_LAUNCH(name, stream, ...)                                  \
+    do {                                                              \
+        ::mc::ProfSpan sp_ = ::mc::prof_begin(name, stream);          \
+        __VA_ARGS__;                                                  \
+        cudaError_t le_ = cudaGetLastError();                         \
+        ::mc::prof_end(sp_, stream);                                  \
+        if (le_ != cudaSuccess)                                       \
+            throw ::mc::Error(MC_E_CUDA, std::string(name) + ": " + cudaGetErrorString(le_)); \
+    } while (0)
+
+// Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
+// neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
+// partial sums are added afterwards.
+constexpr int HUB_CHUNK = 256;
+
+}  // namespace mc
+
+struct mc_graph {
+    int64_t n = 0, nnz = 0, max_degree = 0;
+    int64_t *row_ptr = nullptr;  // device int64[n+1]
+    uint32_t *col = nullptr;     // device uint32[nnz]
+    // hub chunks (device): node, first edge, end edge; per hub, its first chunk
+    int64_t n_chunks = 0, n_hubs = 0;
+    uint32_t *chunk_node = nullptr;
+    int64_t *chunk_e0 = nullptr, *chunk_e1 = nullptr;
+    uint32_t *hub_node = nullptr;
+    int64_t *hub_chunk0 = nullptr;  // n_hubs + 1 entries
+    mc::Arena arena;
+};
+
+struct mc_tables {
+    const mc_graph *g = nullptr;
+    int k = 0, bits = 64;
+    mc::Geometry geo;
+    uint8_t *colors = nullptr;                 // device uint8[n]
+    void *c[mc::MAXK + 1] = {nullptr};         // level h >= 2: n x Wc[h] counts
+    void *S[mc::MAXK + 1] = {nullptr};         // level h <= k-1: n x Ws[h] counts
+    mc::u128 *prefix[mc::MAXK + 1] = {nullptr};  // inclusive node prefix of level totals
+    mc::u128 R[mc::MAXK + 1] = {0};            // rooted totals
+    // merge and gather programs (device)
+    int32_t *m_info[mc::MAXK + 1] = {nullptr};
+    int32_t *m_off[mc::MAXK + 1] = {nullptr};
+    uint32_t *m_terms[mc::MAXK + 1] = {nullptr};
+    int16_t *g_map[mc::MAXK + 1] = {nullptr};
+    mc::Arena arena;
+};

@@ -1,0 +1,907 @@
+// sample.cu -- graphlet classes (Section 4.3.3), uniform and shape-restricted
+// colourful treelet sampling (Section 2.2; sample(T) of Section 4.1), the
+// uniform estimator (Section 2.2) and adaptive graphlet sampling (Algorithm
+// AGS, Section 4.1).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace mc {
+
+void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
+                       cudaStream_t s);
+void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s);
+
+enum : int { SERR_SEARCH = 1, SERR_CLASS = 2 };
+
+// ---------------------------------------------------------------------------
+// Graphlet classes.  Adjacency word of a labelled h-node graph: the pairs
+// (i, j), i < j, in lexicographic order, the first pair in the most
+// significant of the P = C(h,2) bits.  Canonical word: the minimum over all
+// relabelings.  The connected classes of size h are found from those of size
+// h-1 (every connected graph has a node whose removal leaves it connected):
+// each (h-1)-class plus a new node joined to a non-empty node set is
+// canonicalised on the GPU (all h! relabelings per candidate), and the
+// distinct results, ascending, are the class codes.  The lookup table maps
+// every word of a connected graph to its class: one GPU thread per (class,
+// relabeling) writes the relabeled word's entry.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int pair_pos(int h, int i, int j)
+{
+    const int P = h * (h - 1) / 2;
+    return P - 1 - (i * (2 * h - i - 1) / 2 + (j - i - 1));
+}
+
+__device__ __forceinline__ uint32_t relabel_word(uint32_t w, int h, const int *p)
+{
+    // new labels i < j are adjacent when old labels p[i], p[j] are
+    uint32_t out = 0;
+    for (int i = 0; i < h; ++i)
+        for (int j = i + 1; j < h; ++j) {
+            const int a = min(p[i], p[j]), b = max(p[i], p[j]);
+            if ((w >> pair_pos(h, a, b)) & 1u) out |= 1u << pair_pos(h, i, j);
+        }
+    return out;
+}
+
+__global__ void canon_kernel(const uint32_t *cand, int64_t nc, int h, uint32_t *out)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nc;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = cand[t];
+        int p[MAXK], c[MAXK];
+        for (int i = 0; i < h; ++i) { p[i] = i; c[i] = 0; }
+        uint32_t best = relabel_word(w, h, p);
+        int i = 1;
+        while (i < h) {  // Heap's algorithm: every permutation once
+            if (c[i] < i) {
+                const int a = (i & 1) ? c[i] : 0;
+                const int tmp = p[a]; p[a] = p[i]; p[i] = tmp;
+                const uint32_t x = relabel_word(w, h, p);
+                if (x < best) best = x;
+                ++c[i];
+                i = 1;
+            } else {
+                c[i] = 0;
+                ++i;
+            }
+        }
+        out[t] = best;
+    }
+}
+
+__global__ void fill_lut_kernel(const uint32_t *codes, int ncls, int h, int64_t nperm, uint16_t *lut)
+{
+    const int64_t total = (int64_t)ncls * nperm;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int cls = (int)(t / nperm);
+        int64_t r = t - (int64_t)cls * nperm;
+        // permutation number r in the factorial number system
+        int p[MAXK], used = 0;
+        int64_t f = nperm;
+        for (int i = 0; i < h; ++i) {
+            f /= (h - i);
+            int d = (int)(r / f);
+            r -= d * f;
+            int x = 0;
+            for (;; ++x)
+                if (!((used >> x) & 1) && d-- == 0) break;
+            used |= 1 << x;
+            p[i] = x;
+        }
+        lut[relabel_word(codes[cls], h, p)] = (uint16_t)cls;
+    }
+}
+
+struct ClassCatalog {
+    int h = 0;
+    std::vector<uint32_t> codes;
+    uint16_t *lut = nullptr;  // device, 2^C(h,2) entries (0xffff: not connected)
+    bool sigma_ready = false;
+    std::vector<int64_t> sigma_i, sigma_ij;
+};
+
+static std::mutex g_cls_mutex;
+static std::map<std::pair<int, int>, ClassCatalog *> g_cls;
+
+static int64_t factorial(int h)
+{
+    int64_t f = 1;
+    for (int i = 2; i <= h; ++i) f *= i;
+    return f;
+}
+
+static ClassCatalog *class_catalog_locked(int h);
+
+static ClassCatalog *build_classes(int h)
+{
+    ClassCatalog *cc = new ClassCatalog();
+    cc->h = h;
+    const int P = h * (h - 1) / 2;
+    if (h == 1) {
+        cc->codes = {0u};
+    } else {
+        const ClassCatalog *prev = class_catalog_locked(h - 1);
+        std::vector<uint32_t> cand;
+        for (uint32_t R : prev->codes)
+            for (unsigned S = 1; S < (1u << (h - 1)); ++S) {
+                uint32_t w = 0;
+                for (int i = 0; i < h - 1; ++i)
+                    for (int j = i + 1; j < h - 1; ++j)
+                        if ((R >> pair_pos(h - 1, i, j)) & 1u) w |= 1u << pair_pos(h, i, j);
+                for (int i = 0; i < h - 1; ++i)
+                    if ((S >> i) & 1u) w |= 1u << pair_pos(h, i, h - 1);
+                cand.push_back(w);
+            }
+        uint32_t *dc = nullptr, *dout = nullptr;
+        MC_CUDA(cudaMalloc(&dc, cand.size() * 4));
+        MC_CUDA(cudaMalloc(&dout, cand.size() * 4));
+        MC_CUDA(cudaMemcpy(dc, cand.data(), cand.size() * 4, cudaMemcpyHostToDevice));
+        MC_LAUNCH("canon", nullptr, canon_kernel<<<grid_for((int64_t)cand.size(), 128), 128>>>(dc, (int64_t)cand.size(), h, dout));
+        std::vector<uint32_t> canon(cand.size());
+        MC_CUDA(cudaMemcpy(canon.data(), dout, cand.size() * 4, cudaMemcpyDeviceToHost));
+        cudaFree(dc);
+        cudaFree(dout);
+        std::sort(canon.begin(), canon.end());
+        canon.erase(std::unique(canon.begin(), canon.end()), canon.end());
+        cc->codes = canon;
+    }
+    if (cc->codes.size() > 0xffff) throw Error(MC_E_INTERNAL, "too many classes");
+    const size_t nw = (size_t)1 << P;
+    MC_CUDA(cudaMalloc(&cc->lut, nw * sizeof(uint16_t)));
+    MC_CUDA(cudaMemset(cc->lut, 0xff, nw * sizeof(uint16_t)));
+    uint32_t *dcodes = nullptr;
+    MC_CUDA(cudaMalloc(&dcodes, cc->codes.size() * 4));
+    MC_CUDA(cudaMemcpy(dcodes, cc->codes.data(), cc->codes.size() * 4, cudaMemcpyHostToDevice));
+    const int64_t nperm = factorial(h);
+    const int64_t total = (int64_t)cc->codes.size() * nperm;
+    MC_LAUNCH("fill_lut", nullptr, fill_lut_kernel<<<grid_for(total, 256), 256>>>(dcodes, (int)cc->codes.size(), h, nperm, cc->lut));
+    MC_CUDA(cudaDeviceSynchronize());
+    cudaFree(dcodes);
+    return cc;
+}
+
+static ClassCatalog *class_catalog_locked(int h)
+{
+    int dev = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    auto key = std::make_pair(dev, h);
+    auto it = g_cls.find(key);
+    if (it != g_cls.end()) return it->second;
+    ClassCatalog *cc = build_classes(h);
+    g_cls[key] = cc;
+    return cc;
+}
+
+ClassCatalog *class_catalog(int h)
+{
+    if (h < 1 || h > MAXK) throw Error(MC_E_INVALID, "h must be in 1..8");
+    std::lock_guard<std::mutex> lock(g_cls_mutex);
+    return class_catalog_locked(h);
+}
+
+// sigma_ij by the paper's recipe (Section 4.3.3): build the tables of every
+// class graph with each node its own colour; the colourful h-treelets are
+// then exactly the spanning trees.  All classes go through one build, as a
+// disjoint union.
+__global__ void sigma_kernel(const uint64_t *c, int64_t n, int h, int W, const int8_t *unrooted_of,
+                             int nu, unsigned long long *acc)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * W;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / W;
+        const int s = (int)(t - v * W);  // one colour set (all colours) per shape
+        const uint64_t x = c[t];
+        if (x) atomicAdd(&acc[(v / h) * nu + unrooted_of[s]], (unsigned long long)x);
+    }
+}
+
+static void ensure_sigma(ClassCatalog *cc)
+{
+    if (cc->sigma_ready) return;
+    const int h = cc->h;
+    const ShapeCatalog &cat = shape_catalog();
+    const int nu = cat.n_unrooted[h];
+    const int64_t ncls = (int64_t)cc->codes.size();
+    cc->sigma_ij.assign((size_t)ncls * nu, 0);
+    cc->sigma_i.assign((size_t)ncls, 0);
+    if (h == 1) {
+        cc->sigma_ij[0] = 1;
+        cc->sigma_i[0] = 1;
+        cc->sigma_ready = true;
+        return;
+    }
+    // disjoint union: node i of class c is c * h + i, coloured i
+    const int64_t n = ncls * h;
+    std::vector<int64_t> rp((size_t)n + 1, 0);
+    std::vector<uint32_t> col;
+    std::vector<uint8_t> colors((size_t)n);
+    for (int64_t c = 0; c < ncls; ++c)
+        for (int i = 0; i < h; ++i) {
+            const int64_t v = c * h + i;
+            colors[v] = (uint8_t)i;
+            for (int j = 0; j < h; ++j) {
+                if (j == i) continue;
+                const int a = std::min(i, j), b = std::max(i, j);
+                if ((cc->codes[c] >> pair_pos(h, a, b)) & 1u) col.push_back((uint32_t)(c * h + j));
+            }
+            rp[v + 1] = (int64_t)col.size();
+        }
+    mc_graph *g = nullptr;
+    mc_tables *t = nullptr;
+    mc_status st = mc_load_graph(n, (int64_t)col.size(), rp.data(), col.data(), MC_GRAPH_TRUSTED, nullptr,
+                                 nullptr, &g);
+    if (st != MC_OK) throw Error(st, "sigma: load graph failed");
+    uint8_t *dcol = nullptr;
+    MC_CUDA(cudaMalloc(&dcol, (size_t)n));
+    MC_CUDA(cudaMemcpy(dcol, colors.data(), (size_t)n, cudaMemcpyHostToDevice));
+    st = mc_build_tables(g, dcol, h, 64, 0, nullptr, nullptr, &t);
+    cudaFree(dcol);
+    if (st != MC_OK) { mc_free_graph(g); throw Error(st, "sigma: build failed"); }
+    std::vector<int8_t> uo(cat.r[h]);
+    for (int s = 0; s < cat.r[h]; ++s) uo[s] = (int8_t)cat.shapes[cat.gid(h, s)].unrooted;
+    int8_t *duo = nullptr;
+    unsigned long long *dacc = nullptr;
+    MC_CUDA(cudaMalloc(&duo, uo.size()));
+    MC_CUDA(cudaMalloc(&dacc, (size_t)ncls * nu * 8));
+    MC_CUDA(cudaMemcpy(duo, uo.data(), uo.size(), cudaMemcpyHostToDevice));
+    MC_CUDA(cudaMemset(dacc, 0, (size_t)ncls * nu * 8));
+    const int W = t->geo.Wc[h];  // = r_h: one colour set
+    MC_LAUNCH("sigma", nullptr, sigma_kernel<<<grid_for(n * W, 256), 256>>>((const uint64_t *)t->c[h], n, h, W, duo, nu, dacc));
+    std::vector<unsigned long long> acc((size_t)ncls * nu);
+    MC_CUDA(cudaMemcpy(acc.data(), dacc, acc.size() * 8, cudaMemcpyDeviceToHost));
+    cudaFree(duo);
+    cudaFree(dacc);
+    mc_free_tables(t);
+    mc_free_graph(g);
+    for (int64_t c = 0; c < ncls; ++c)
+        for (int j = 0; j < nu; ++j) {
+            const unsigned long long x = acc[(size_t)c * nu + j];
+            if (x % (unsigned long long)h) throw Error(MC_E_INTERNAL, "sigma: rooted count not divisible by h");
+            cc->sigma_ij[(size_t)c * nu + j] = (int64_t)(x / h);
+            cc->sigma_i[(size_t)c] += (int64_t)(x / h);
+        }
+    cc->sigma_ready = true;
+}
+
+ClassCatalog *class_catalog_sigma(int h)
+{
+    ClassCatalog *cc = class_catalog(h);
+    std::lock_guard<std::mutex> lock(g_cls_mutex);
+    ensure_sigma(cc);
+    return cc;
+}
+
+// ---------------------------------------------------------------------------
+// Sampler: one warp per sample.
+//   step 0  X = uniform(R); v = first node whose inclusive prefix exceeds X
+//           (32-ary warp search); (T, C) = first entry of v's level-h row,
+//           in (shape id, colour mask) order, whose running sum exceeds the
+//           remainder (warp scan);
+//   step s  for each decomposition node (T, C, x) in pre-order (T' before
+//           T''): Y = uniform(beta_T c(T_C, x)); the block of colour sets
+//           C'' (ascending mask) is found from the block weights
+//           c(T'_{C\C''}, x) S(T'', C'', x); inside it, the neighbour u
+//           (ascending) is the first whose running sum of c(T''_{C''}, u)
+//           exceeds floor(Y' / c(T'_{C\C''}, x)) -- the same pair as a flat
+//           scan over (C'', u) with weights c(T') c(T'').
+// The h leaves of the decomposition are the sample's nodes; their induced
+// subgraph is classified by the lookup table.
+// ---------------------------------------------------------------------------
+struct SampleArgs {
+    const int64_t *row_ptr;
+    const uint32_t *col;
+    const uint8_t *colors;
+    int64_t n;
+    const void *c[MAXK + 1];
+    const void *S[MAXK + 1];
+    int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
+    int k, h;
+    const u128 *prefix;
+    u128 R;
+    uint64_t allow0, allow1;
+    int first[MAXK + 2];
+    uint8_t sz[MAX_SHAPES], loc[MAX_SHAPES], lft[MAX_SHAPES], rgt[MAX_SHAPES], beta[MAX_SHAPES];
+    uint8_t crank[1 << (MAXK - 1)];
+    uint8_t pi[28], pj[28];
+    uint64_t seed, first_index;
+    int64_t count;
+    const uint16_t *lut;
+    uint32_t *nodes, *roots;
+    int32_t *shapes, *classes;
+    unsigned long long *hist;
+    int ncls;
+    int *err;
+};
+
+template <typename CT>
+__device__ __forceinline__ u128 count_at(const SampleArgs &a, int g, unsigned C, uint32_t x, int cx)
+{
+    const int hg = a.sz[g];
+    if (hg == 1) return 1;
+    const unsigned rel = drop_colour(C & ~(1u << cx), cx);
+    const CT *row = (const CT *)a.c[hg] + (int64_t)x * a.Wc[hg];
+    return widen(row[a.loc[g] * a.Bc[hg] + a.crank[rel]]);
+}
+
+// k-th set bit (0-based) positions of `rest` selected by index mask `im`
+__device__ __forceinline__ unsigned deposit(unsigned im, unsigned rest)
+{
+    unsigned out = 0;
+    for (int i = 0; rest; ++i) {
+        const unsigned low = rest & (0u - rest);
+        if ((im >> i) & 1u) out |= low;
+        rest &= rest - 1;
+    }
+    return out;
+}
+
+// i-th (0-based) index mask of popcount m over nb bits in ascending order
+__device__ __forceinline__ unsigned nth_subset(int nb, int m, int i)
+{
+    for (unsigned x = 0; x < (1u << nb); ++x)
+        if (__popc(x) == m && i-- == 0) return x;
+    return 0;
+}
+
+__device__ __forceinline__ bool adjacent(const int64_t *row_ptr, const uint32_t *col, uint32_t a, uint32_t b)
+{
+    int64_t lo = row_ptr[a], hi = row_ptr[a + 1];
+    const int64_t lb = row_ptr[b], hb = row_ptr[b + 1];
+    if (hb - lb < hi - lo) { lo = lb; hi = hb; b = a; }
+    const int64_t end = hi;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo < end && col[lo] == b;
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleArgs a)
+{
+    extern __shared__ unsigned int s_hist[];
+    if (a.hist) {
+        for (int i = threadIdx.x; i < a.ncls; i += blockDim.x) s_hist[i] = 0;
+        __syncthreads();
+    }
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int h = a.h;
+    bool bad = false;
+    for (int64_t sid = warp; sid < a.count; sid += nwarps) {
+        const uint64_t index = a.first_index + (uint64_t)sid;
+        // ---- root node
+        u128 X;
+        if (!draw_below(a.seed, index, 0, a.R, X)) { bad = true; continue; }
+        int64_t lo = 0, hi = a.n;
+        while (hi - lo > 32) {
+            const int64_t step = (hi - lo + 31) >> 5;
+            int64_t probe = lo + (lane + 1) * step - 1;
+            if (probe > hi - 1) probe = hi - 1;
+            const unsigned m = __ballot_sync(FULL, a.prefix[probe] > X);
+            const int f = m ? __ffs(m) - 1 : 31;
+            const int64_t nlo = lo + f * step;
+            const int64_t nhi = min(hi, lo + (f + 1) * step);
+            lo = nlo;
+            hi = nhi;
+        }
+        const int64_t cand = lo + lane;
+        const unsigned mv = __ballot_sync(FULL, cand < hi && a.prefix[cand] > X);
+        if (!mv) { bad = true; continue; }
+        const uint32_t v = (uint32_t)(lo + __ffs(mv) - 1);
+        const u128 rem = X - (v ? a.prefix[v - 1] : (u128)0);
+        // ---- entry of v's level-h row
+        const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
+        int found = -1;
+        {
+            u128 run = 0;
+            for (int b = 0; b < a.Wc[h]; b += 32) {
+                const int e = b + lane;
+                u128 val = 0;
+                if (e < a.Wc[h]) {
+                    const int sh = e / a.Bc[h];
+                    const bool ok = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
+                    if (ok) val = widen(vrow[e]);
+                }
+                const u128 cum = warp_inclusive_scan(val) + run;
+                const unsigned m = __ballot_sync(FULL, cum > rem);
+                if (m) { found = b + __ffs(m) - 1; break; }
+                run = shfl(cum, 31);
+            }
+        }
+        if (found < 0) { bad = true; continue; }
+        const int cv0 = a.colors[v];
+        const int s0 = found / a.Bc[h];
+        const unsigned C0 = (1u << cv0) | insert_colour_gap(nth_subset(a.k - 1, h - 1, found % a.Bc[h]), cv0);
+        // ---- descent
+        int stg[MAXK], sp = 0, nn = 0;
+        unsigned stC[MAXK];
+        uint32_t stx[MAXK], nodes[MAXK];
+        stg[0] = a.first[h] + s0; stC[0] = C0; stx[0] = v; sp = 1;
+        uint32_t step = 0;
+        while (sp > 0) {
+            --sp;
+            const int g = stg[sp];
+            const unsigned C = stC[sp];
+            const uint32_t x = stx[sp];
+            if (a.sz[g] == 1) {
+                if (nn >= MAXK) { bad = true; break; }
+                nodes[nn++] = x;
+                continue;
+            }
+            ++step;
+            const int cx = a.colors[x];
+            const int ga = a.lft[g], gb = a.rgt[g];
+            const int hb = a.sz[gb];
+            const u128 W = (u128)a.beta[g] * count_at<CT>(a, g, C, x, cx);
+            u128 Y;
+            if (!draw_below(a.seed, index, step, W, Y)) { bad = true; break; }
+            const unsigned rest = C & ~(1u << cx);
+            const int nr = __popc(rest);
+            const int nsub = [&] { int r = 1; for (int i = 1; i <= hb; ++i) r = r * (nr - hb + i) / i; return r; }();
+            // block of C''
+            int blk = -1;
+            u128 before = 0, run = 0;
+            unsigned C2 = 0;
+            for (int b = 0; b < nsub; b += 32) {
+                const int i = b + lane;
+                u128 wgt = 0;
+                unsigned c2 = 0;
+                if (i < nsub) {
+                    c2 = deposit(nth_subset(nr, hb, i), rest);
+                    const u128 x1 = count_at<CT>(a, ga, C & ~c2, x, cx);
+                    const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
+                    wgt = x1 * widen(srow[a.loc[gb] * a.Bs[hb] + a.crank[drop_colour(c2, cx)]]);
+                }
+                const u128 cum = warp_inclusive_scan(wgt) + run;
+                const unsigned m = __ballot_sync(FULL, cum > Y);
+                if (m) {
+                    const int f = __ffs(m) - 1;
+                    blk = b + f;
+                    before = shfl(cum, f) - shfl(wgt, f);
+                    C2 = __shfl_sync(FULL, c2, f);
+                    break;
+                }
+                run = shfl(cum, 31);
+            }
+            if (blk < 0) { bad = true; break; }
+            const unsigned C1 = C & ~C2;
+            const u128 x1 = count_at<CT>(a, ga, C1, x, cx);
+            const u128 Yp = Y - before;
+            const u128 q = ((Yp >> 64) == 0 && (x1 >> 64) == 0) ? (u128)((uint64_t)Yp / (uint64_t)x1) : Yp / x1;
+            // neighbour
+            const int64_t e0 = a.row_ptr[x], e1 = a.row_ptr[x + 1];
+            int64_t sel = -1;
+            run = 0;
+            const int lb = a.loc[gb];
+            for (int64_t b = e0; b < e1; b += 32) {
+                const int64_t e = b + lane;
+                u128 val = 0;
+                if (e < e1) {
+                    const uint32_t u = a.col[e];
+                    const int cu = a.colors[u];
+                    if ((C2 >> cu) & 1u) {
+                        if (hb == 1) val = 1;
+                        else {
+                            const CT *urow = (const CT *)a.c[hb] + (int64_t)u * a.Wc[hb];
+                            val = widen(urow[lb * a.Bc[hb] + a.crank[drop_colour(C2 & ~(1u << cu), cu)]]);
+                        }
+                    }
+                }
+                const u128 cum = warp_inclusive_scan(val) + run;
+                const unsigned m = __ballot_sync(FULL, cum > q);
+                if (m) { sel = b + __ffs(m) - 1; break; }
+                run = shfl(cum, 31);
+            }
+            if (sel < 0) { bad = true; break; }
+            const uint32_t u = a.col[sel];
+            if (sp + 2 > MAXK) { bad = true; break; }
+            stg[sp] = gb; stC[sp] = C2; stx[sp] = u; ++sp;
+            stg[sp] = ga; stC[sp] = C1; stx[sp] = x; ++sp;
+        }
+        if (nn != h) { bad = true; continue; }
+        for (int i = 1; i < h; ++i)
+            for (int j = i; j > 0 && nodes[j - 1] > nodes[j]; --j) {
+                const uint32_t tmp = nodes[j]; nodes[j] = nodes[j - 1]; nodes[j - 1] = tmp;
+            }
+        // ---- classify: lane p tests pair p
+        const int P = h * (h - 1) / 2;
+        bool adj = false;
+        if (lane < P) adj = adjacent(a.row_ptr, a.col, nodes[a.pi[lane]], nodes[a.pj[lane]]);
+        const unsigned bal = __ballot_sync(FULL, adj);
+        const uint32_t word = __brev(bal) >> (32 - P);
+        const int cls = a.lut[word];
+        if (cls == 0xffff) bad = true;
+        if (lane == 0) {
+            if (a.nodes) for (int i = 0; i < h; ++i) a.nodes[sid * h + i] = nodes[i];
+            if (a.roots) a.roots[sid] = v;
+            if (a.shapes) a.shapes[sid] = s0;
+            if (a.classes) a.classes[sid] = cls == 0xffff ? -1 : cls;
+            if (a.hist && cls != 0xffff) atomicAdd(&s_hist[cls], 1u);
+        }
+    }
+    if (bad) atomicOr(a.err, SERR_SEARCH);
+    if (a.hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.ncls; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(&a.hist[i], (unsigned long long)s_hist[i]);
+    }
+}
+
+// Uniform estimator (Section 2.2): g_i = ((t * hits_i) / (sigma_i * N)) * (1/p),
+// one correctly rounded operation at a time.
+__global__ void uniform_estimate_kernel(const unsigned long long *hits, const int64_t *sigma, int ncls,
+                                        u128 t, int64_t N, double inv_p, double *est)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncls) return;
+    const double td = u128_to_double(t);
+    const double num = __dmul_rn(td, __ull2double_rn(hits[i]));
+    const double den = __dmul_rn(__ll2double_rn(sigma[i]), __ll2double_rn(N));
+    est[i] = __dmul_rn(__ddiv_rn(num, den), inv_p);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
+{
+    const ShapeCatalog &cat = shape_catalog();
+    const mc_graph *g = t->g;
+    a = SampleArgs{};
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.colors = t->colors;
+    a.n = g->n;
+    for (int i = 1; i <= t->k; ++i) {
+        a.c[i] = t->c[i];
+        a.S[i] = t->S[i];
+        a.Bc[i] = t->geo.Bc[i];
+        a.Bs[i] = t->geo.Bs[i];
+        a.Wc[i] = t->geo.Wc[i];
+        a.Ws[i] = t->geo.Ws[i];
+    }
+    a.k = t->k;
+    a.h = h;
+    for (int i = 0; i <= MAXK + 1; ++i) a.first[i] = cat.first[std::min(i, MAXK + 1)];
+    for (int gid = 0; gid < cat.first[t->k + 1]; ++gid) {
+        const Shape &s = cat.shapes[gid];
+        a.sz[gid] = (uint8_t)s.size;
+        a.loc[gid] = (uint8_t)s.local;
+        a.lft[gid] = (uint8_t)std::max(s.left, 0);
+        a.rgt[gid] = (uint8_t)std::max(s.right, 0);
+        a.beta[gid] = (uint8_t)s.beta;
+    }
+    for (unsigned m = 0; m < (1u << (t->k - 1)); ++m) a.crank[m] = (uint8_t)colex_rank(m);
+    int p = 0;
+    for (int i = 0; i < h; ++i)
+        for (int j = i + 1; j < h; ++j) { a.pi[p] = (uint8_t)i; a.pj[p] = (uint8_t)j; ++p; }
+}
+
+struct RootIndex {
+    const u128 *prefix = nullptr;
+    u128 R = 0;
+};
+
+static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scratch, int *err, cudaStream_t s,
+                            uint64_t &allow0, uint64_t &allow1)
+{
+    const ShapeCatalog &cat = shape_catalog();
+    allow0 = allow1 = 0;
+    for (int i = 0; i < cat.r[h]; ++i)
+        if (unrooted < 0 || cat.shapes[cat.gid(h, i)].unrooted == unrooted) {
+            if (i < 64) allow0 |= 1ull << i; else allow1 |= 1ull << (i - 64);
+        }
+    RootIndex ri;
+    if (unrooted < 0) {
+        ri.prefix = t->prefix[h];
+        ri.R = t->R[h];
+        return ri;
+    }
+    u128 *p = scratch.get<u128>((size_t)t->g->n);
+    launch_row_totals(t, h, allow0, allow1, p, err, s);
+    inclusive_scan_u128(p, t->g->n, err, scratch, s);
+    MC_CUDA(cudaMemcpyAsync(&ri.R, p + (t->g->n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    ri.prefix = p;
+    return ri;
+}
+
+static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
+{
+    const int block = 256;
+    int64_t grid = (a.count * 32 + block - 1) / block;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    const size_t smem = a.hist ? (size_t)a.ncls * sizeof(unsigned int) : 0;
+    if (t->bits == 64) {
+        if (smem > 48 * 1024)
+            MC_CUDA(cudaFuncSetAttribute(sample_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MC_LAUNCH("sample", s, sample_kernel<uint64_t><<<(unsigned)grid, block, smem, s>>>(a));
+    } else {
+        if (smem > 48 * 1024)
+            MC_CUDA(cudaFuncSetAttribute(sample_kernel<u128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MC_LAUNCH("sample", s, sample_kernel<u128><<<(unsigned)grid, block, smem, s>>>(a));
+    }
+}
+
+static double inv_colourful_prob(int k, int h)
+{
+    double num = 1.0, den = 1.0;
+    for (int i = 0; i < h; ++i) num *= (double)k;
+    for (int i = 1; i <= k - h; ++i) num *= (double)i;
+    for (int i = 1; i <= k; ++i) den *= (double)i;
+    return num / den;
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+extern "C" int mc_num_shapes(int h)
+{
+    if (h < 1 || h > MAXK) return -1;
+    return shape_catalog().r[h];
+}
+
+extern "C" int mc_num_unrooted(int h)
+{
+    if (h < 1 || h > MAXK) return -1;
+    return shape_catalog().n_unrooted[h];
+}
+
+extern "C" int mc_num_classes(int h)
+{
+    int out = -1;
+    mc_status st = guarded([&] { out = (int)class_catalog(h)->codes.size(); });
+    return st == MC_OK ? out : -1;
+}
+
+extern "C" mc_status mc_shape_info(int h, uint32_t *code, int32_t *unrooted, int32_t *beta, int32_t *left,
+                                   int32_t *right)
+{
+    return guarded([&] {
+        MC_REQUIRE(h >= 1 && h <= MAXK, "h must be in 1..8");
+        const ShapeCatalog &cat = shape_catalog();
+        for (int i = 0; i < cat.r[h]; ++i) {
+            const Shape &s = cat.shapes[cat.gid(h, i)];
+            if (code) code[i] = s.code;
+            if (unrooted) unrooted[i] = s.unrooted;
+            if (beta) beta[i] = s.beta;
+            if (left) left[i] = s.left < 0 ? -1 : cat.shapes[s.left].local;
+            if (right) right[i] = s.right < 0 ? -1 : cat.shapes[s.right].local;
+        }
+    });
+}
+
+extern "C" mc_status mc_class_codes(int h, uint32_t *codes)
+{
+    return guarded([&] {
+        MC_REQUIRE(codes, "codes is NULL");
+        const ClassCatalog *cc = class_catalog(h);
+        std::copy(cc->codes.begin(), cc->codes.end(), codes);
+    });
+}
+
+extern "C" mc_status mc_sigma(int h, int64_t *sigma_i, int64_t *sigma_ij)
+{
+    return guarded([&] {
+        const ClassCatalog *cc = class_catalog_sigma(h);
+        if (sigma_i) std::copy(cc->sigma_i.begin(), cc->sigma_i.end(), sigma_i);
+        if (sigma_ij) std::copy(cc->sigma_ij.begin(), cc->sigma_ij.end(), sigma_ij);
+    });
+}
+
+extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
+                               uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
+                               int32_t *shapes, int32_t *classes, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t, "tables is NULL");
+        MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(count >= 0, "count must be >= 0");
+        MC_REQUIRE(unrooted_shape < shape_catalog().n_unrooted[h], "unrooted shape out of range");
+        if (count == 0) return;
+        cudaStream_t s = (cudaStream_t)stream;
+        const ClassCatalog *cc = class_catalog(h);
+        Arena scratch;
+        scratch.alloc = t->arena.alloc;
+        scratch.stream = s;
+        int *err = scratch.get<int>(2);
+        MC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+        SampleArgs a;
+        fill_sample_args(a, t, h);
+        RootIndex ri = root_index(t, h, unrooted_shape, scratch, err + 1, s, a.allow0, a.allow1);
+        if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of the requested size/shape");
+        a.prefix = ri.prefix;
+        a.R = ri.R;
+        a.seed = seed;
+        a.first_index = first_index;
+        a.count = count;
+        a.lut = cc->lut;
+        a.nodes = nodes;
+        a.roots = roots;
+        a.shapes = shapes;
+        a.classes = classes;
+        a.hist = nullptr;
+        a.ncls = (int)cc->codes.size();
+        a.err = err;
+        launch_sampler(t, a, s);
+        int herr[2] = {0, 0};
+        MC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
+    });
+}
+
+extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *p, double *est,
+                                        uint64_t *hits, mc_estimate_stats *stats, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t && p && est && hits, "NULL argument");
+        const int h = p->h;
+        MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(p->samples >= 0, "samples must be >= 0");
+        MC_REQUIRE(p->mode == MC_EST_UNIFORM || p->mode == MC_EST_AGS, "unknown mode");
+        cudaStream_t s = (cudaStream_t)stream;
+        const ClassCatalog *cc = class_catalog_sigma(h);
+        const int ncls = (int)cc->codes.size();
+        const ShapeCatalog &cat = shape_catalog();
+        Arena scratch;
+        scratch.alloc = t->arena.alloc;
+        scratch.stream = s;
+        int *err = scratch.get<int>(2);
+        MC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
+        mc_estimate_stats st{};
+        const double ip = inv_colourful_prob(t->k, h);
+        if (p->mode == MC_EST_UNIFORM) {
+            MC_REQUIRE(p->samples > 0, "uniform estimation needs samples > 0");
+            unsigned long long *dh = scratch.get<unsigned long long>((size_t)ncls);
+            int64_t *dsig = scratch.get<int64_t>((size_t)ncls);
+            double *dest = scratch.get<double>((size_t)ncls);
+            MC_CUDA(cudaMemsetAsync(dh, 0, (size_t)ncls * 8, s));
+            MC_CUDA(cudaMemcpyAsync(dsig, cc->sigma_i.data(), (size_t)ncls * 8, cudaMemcpyHostToDevice, s));
+            SampleArgs a;
+            fill_sample_args(a, t, h);
+            RootIndex ri = root_index(t, h, -1, scratch, err + 1, s, a.allow0, a.allow1);
+            if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
+            a.prefix = ri.prefix;
+            a.R = ri.R;
+            a.seed = p->seed;
+            a.first_index = p->first_index;
+            a.count = p->samples;
+            a.lut = cc->lut;
+            a.hist = dh;
+            a.ncls = ncls;
+            a.err = err;
+            launch_sampler(t, a, s);
+            MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, ri.R / (u128)h, p->samples, ip, dest));
+            std::vector<unsigned long long> hh((size_t)ncls);
+            MC_CUDA(cudaMemcpyAsync(hh.data(), dh, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(est, dest, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
+            int herr[2] = {0, 0};
+            MC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
+            for (int i = 0; i < ncls; ++i) hits[i] = hh[i];
+            st.samples = p->samples;
+            st.batches = 1;
+        } else {
+            // Algorithm AGS with batched speculative sampling: a batch of
+            // samples is drawn from the current treelet T_j; the host replays
+            // it in order and cuts it at the first newly covered graphlet,
+            // which makes the outcome identical to one sample at a time.
+            int64_t cbar = p->cbar;
+            if (cbar <= 0) {
+                MC_REQUIRE(p->eps > 0 && p->delta > 0 && p->delta < 1, "AGS needs cbar or (eps, delta)");
+                cbar = (int64_t)std::ceil(4.0 / (p->eps * p->eps) * std::log(2.0 * ncls / p->delta));
+            }
+            const int nu = cat.n_unrooted[h];
+            std::vector<u128> tj(nu);
+            std::vector<double> tjd(nu);
+            std::vector<RootIndex> ris(nu);
+            std::vector<std::pair<uint64_t, uint64_t>> allows(nu);
+            for (int j = 0; j < nu; ++j) {
+                uint64_t rooted[2], un[2];
+                mc_status s2 = mc_total(t, h, j, rooted, un, stream);
+                if (s2 != MC_OK) throw Error(s2, "AGS: treelet totals failed");
+                tj[j] = (u128)un[0] | ((u128)un[1] << 64);
+                tjd[j] = (double)tj[j];
+            }
+            int cur = -1;
+            for (int j = 0; j < nu; ++j)
+                if (tj[j] > 0 && (cur < 0 || tj[j] > tj[cur])) cur = j;
+            std::vector<int64_t> nj(nu, 0);
+            std::vector<uint64_t> hv((size_t)ncls, 0);
+            std::vector<double> w((size_t)ncls, 0.0);
+            std::vector<uint8_t> covered((size_t)ncls, 0);
+            int64_t drawn = 0, ncov = 0;
+            const int64_t bmin = p->batch > 0 ? p->batch : 65536;
+            int64_t B = bmin;
+            const int64_t bmax = p->batch > 0 ? p->batch : (int64_t)1 << 22;
+            int32_t *dcls = scratch.get<int32_t>((size_t)bmax);
+            std::vector<int32_t> hcls((size_t)bmax);
+            auto weights = [&] {
+                for (int i = 0; i < ncls; ++i) {
+                    double acc = 0.0;
+                    for (int j = 0; j < nu; ++j)
+                        if (tj[j] > 0) acc += (double)(nj[j] * cc->sigma_ij[(size_t)i * nu + j]) / tjd[j];
+                    w[i] = acc;
+                }
+            };
+            while (cur >= 0 && ncov < ncls && drawn < p->samples) {
+                if (!ris[cur].prefix) {
+                    ris[cur] = root_index(t, h, cur, scratch, err + 1, s, allows[cur].first, allows[cur].second);
+                }
+                const int64_t b = std::min(B, p->samples - drawn);
+                SampleArgs a;
+                fill_sample_args(a, t, h);
+                a.allow0 = allows[cur].first;
+                a.allow1 = allows[cur].second;
+                a.prefix = ris[cur].prefix;
+                a.R = ris[cur].R;
+                a.seed = p->seed;
+                a.first_index = p->first_index + (uint64_t)drawn;
+                a.count = b;
+                a.lut = cc->lut;
+                a.classes = dcls;
+                a.ncls = ncls;
+                a.err = err;
+                launch_sampler(t, a, s);
+                MC_CUDA(cudaMemcpyAsync(hcls.data(), dcls, (size_t)b * 4, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaStreamSynchronize(s));
+                st.batches++;
+                bool switched = false;
+                for (int64_t q = 0; q < b; ++q) {
+                    const int i = hcls[(size_t)q];
+                    if (i < 0 || i >= ncls) throw Error(MC_E_INTERNAL, "AGS: bad class id");
+                    nj[cur]++;
+                    drawn++;
+                    hv[(size_t)i]++;
+                    if ((int64_t)hv[(size_t)i] == cbar && !covered[(size_t)i]) {
+                        covered[(size_t)i] = 1;
+                        ncov++;
+                        st.switches++;
+                        weights();
+                        int best = -1;
+                        double bestv = 0.0;
+                        for (int j = 0; j < nu; ++j) {
+                            if (tj[j] == 0) continue;
+                            double acc = 0.0;
+                            for (int a2 = 0; a2 < ncls; ++a2)
+                                if (covered[(size_t)a2])
+                                    acc += ((double)cc->sigma_ij[(size_t)a2 * nu + j] * (double)hv[(size_t)a2]) / w[(size_t)a2];
+                            const double val = acc / tjd[j];
+                            if (best < 0 || val < bestv) { best = j; bestv = val; }
+                        }
+                        cur = best;
+                        st.discarded += b - q - 1;
+                        switched = true;
+                        break;
+                    }
+                }
+                B = switched ? bmin : std::min(2 * B, bmax);
+            }
+            weights();
+            for (int i = 0; i < ncls; ++i) {
+                hits[i] = hv[(size_t)i];
+                est[i] = w[(size_t)i] > 0.0 ? ((double)hv[(size_t)i] / w[(size_t)i]) * ip : 0.0;
+            }
+            int herr[2] = {0, 0};
+            MC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
+            st.samples = drawn;
+            st.covered = ncov;
+        }
+        if (stats) *stats = st;
+    });
+}

@@ -1,0 +1,52 @@
+"""CPU-side checks of the CUDA library: it loads, exports every symbol the
+C header declares, and its host-side shape catalogue agrees with the
+oracle's (no device calls)."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from oracle import catalog as cat
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def motif():
+    import paper_2009_03052_gb300 as M
+    M.build()
+    M.load()
+    return M
+
+
+def test_exports_every_declared_symbol(motif):
+    header = open(os.path.join(ROOT, "include", "motif.h")).read()
+    declared = set(re.findall(r"\b(mc_[a-z_0-9]+)\s*\(", header))
+    lib = motif.load()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(motif.EXPORTED)
+
+
+def test_shape_catalogue_matches_oracle(motif):
+    for h in range(1, 9):
+        info = motif.shape_info(h)
+        shapes = cat.rooted_shapes(h)
+        assert motif.num_shapes(h) == len(shapes)
+        assert motif.num_unrooted(h) == len(cat.unrooted_shapes(h))
+        for i, s in enumerate(shapes):
+            assert int(info["code"][i]) == (int(s, 2) if s else 0)
+            assert int(info["unrooted"][i]) == cat.unrooted_id(s)
+            if h > 1:
+                a, b, beta = cat.decompose(s)
+                assert int(info["beta"][i]) == beta
+                assert int(info["left"][i]) == cat.shape_id(a)
+                assert int(info["right"][i]) == cat.shape_id(b)
+
+
+def test_errors_without_device(motif):
+    # argument checks happen before any device work
+    st = motif.load().mc_build_tables(None, None, 4, 64, 0, None, None, None)
+    assert st == motif.MC_E_INVALID
+    assert b"NULL" in motif.load().mc_last_error()
