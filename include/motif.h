@@ -174,6 +174,30 @@ typedef struct {
 mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *params, double *est,
                              uint64_t *hits, mc_estimate_stats *stats, void *stream);
 
+/* Uniform estimation that allocates no device memory, for callers that
+ * cannot allocate: code running while a stream is being captured into a CUDA
+ * graph (cudaMalloc is not allowed there), serving loops that hand every
+ * byte of device memory to their own pool up front, and latency-critical
+ * loops that must not hit cudaMalloc's implicit synchronisation.  The paper
+ * has no counterpart: it computes the same result as mc_estimate_counts in
+ * MC_EST_UNIFORM mode (same samples, same hits, same estimates).
+ *  - Its device scratch (histogram, sigma and estimate arrays, error flags)
+ *    is one static array of the library, sized for at most 12288 graphlet
+ *    classes (about 290 KB), which every GPU that loads the library holds
+ *    until the process exits.  Classes beyond that limit give
+ *    MC_E_UNSUPPORTED (the largest supported size, h = 8, has 11117).
+ *  - The first call on a device looks up that array's device address (no
+ *    allocation); make that first call before any stream capture.
+ *  - The graphlet catalogue of size h must already exist on the device
+ *    (mc_sigma(h), mc_num_classes(h) with mc_sigma, or mc_estimate_counts
+ *    create it); otherwise MC_E_INVALID, since creating it allocates.
+ *  - All calls share the one scratch array, cleared at the start of each
+ *    call: calls whose work overlaps on the GPU (other streams, other host
+ *    threads) race and must be serialised by the caller.
+ * est, hits: host arrays of mc_num_classes(h).  Synchronises `stream`. */
+mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint64_t seed, uint64_t first_index,
+                                      int64_t samples, double *est, uint64_t *hits, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Catalogue (computed on the current device on first use, then cached)      */
 /* ------------------------------------------------------------------------ */

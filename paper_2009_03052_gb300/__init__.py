@@ -32,7 +32,7 @@ EXPORTED = [
     "mc_free_tables", "mc_total", "mc_table_layout", "mc_read_table", "mc_sample",
     "mc_estimate_counts", "mc_num_shapes", "mc_num_unrooted", "mc_num_classes", "mc_shape_info",
     "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
-    "mc_profile_read", "mc_launch_count",
+    "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         lib.mc_profile_enable.argtypes = [C.c_int]
         lib.mc_profile_read.argtypes = [P, C.c_size_t, P, P, C.c_int, C.POINTER(C.c_int)]
         lib.mc_launch_count.restype = C.c_int64
+        lib.mc_estimate_uniform_noalloc.argtypes = [P, C.c_int, u64, u64, i64, P, P, P]
         _lib = lib
         return lib
 
@@ -305,6 +306,17 @@ class Tables:
         return est, hits, {"samples": st.samples, "switches": st.switches,
                            "covered": st.covered, "batches": st.batches,
                            "discarded": st.discarded}
+    def estimate_noalloc(self, h: int, seed: int, samples: int, first_index: int = 0,
+                         stream=None):
+        """mc_estimate_uniform_noalloc: the uniform estimate without any
+        device allocation (for callers that cannot allocate); the graphlet
+        catalogue of size h must exist (sigma(h) creates it)."""
+        ncls = num_classes(h)
+        est = np.zeros(ncls, np.float64)
+        hits = np.zeros(ncls, np.uint64)
+        _check(load().mc_estimate_uniform_noalloc(self.handle, h, seed, first_index, samples,
+                                                  _ptr(est), _ptr(hits), _stream_ptr(stream)))
+        return est, hits
 
 
 # ---------------------------------------------------------------------------

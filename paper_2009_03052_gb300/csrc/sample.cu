@@ -905,3 +905,106 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         if (stats) *stats = st;
     });
 }
+
+// ---------------------------------------------------------------------------
+// Uniform estimation without device allocation: the scratch of
+// mc_estimate_counts' uniform mode (histogram, sigma, estimates, error
+// flags) lives in one static device array instead of allocator memory.
+// ---------------------------------------------------------------------------
+namespace mc {
+
+constexpr int NOALLOC_MAX_CLASSES = 12288;  // >= 11117, the connected 8-node graphs
+
+struct NoAllocScratch {
+    unsigned long long hist[NOALLOC_MAX_CLASSES];
+    int64_t sigma[NOALLOC_MAX_CLASSES];
+    double est[NOALLOC_MAX_CLASSES];
+    int err[4];
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+static std::mutex g_noalloc_mutex;
+static std::map<int, NoAllocScratch *> g_noalloc_addr;
+
+// Device address of the static scratch on the current device, looked up
+// once per device (host code cannot use the symbol itself as a pointer).
+static NoAllocScratch *noalloc_scratch()
+{
+    int dev = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) return it->second;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        throw Error(MC_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = (NoAllocScratch *)p;
+    return (NoAllocScratch *)p;
+}
+
+// The class catalogue of size h if it already exists with sigma, else NULL
+// (never builds it: that would allocate).
+static const ClassCatalog *existing_catalogue(int h)
+{
+    int dev = 0;
+    MC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_cls_mutex);
+    auto it = g_cls.find(std::make_pair(dev, h));
+    if (it == g_cls.end() || !it->second->sigma_ready) return nullptr;
+    return it->second;
+}
+
+}  // namespace mc
+
+extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint64_t seed, uint64_t first_index,
+                                                 int64_t samples, double *est, uint64_t *hits, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t && est && hits, "NULL argument");
+        MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(samples > 0, "samples must be > 0");
+        const ClassCatalog *cc = existing_catalogue(h);
+        if (!cc)
+            throw Error(MC_E_INVALID, "the graphlet catalogue of this size does not exist on this device yet "
+                                      "(creating it allocates); call mc_sigma(h) first");
+        const int ncls = (int)cc->codes.size();
+        if (ncls > NOALLOC_MAX_CLASSES)
+            throw Error(MC_E_UNSUPPORTED, "more graphlet classes than the static scratch holds (" +
+                                              std::to_string(NOALLOC_MAX_CLASSES) + ")");
+        if (t->R[h] == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
+        cudaStream_t s = (cudaStream_t)stream;
+        NoAllocScratch *scr = noalloc_scratch();
+        MC_CUDA(cudaMemsetAsync(scr->hist, 0, (size_t)ncls * sizeof(unsigned long long), s));
+        MC_CUDA(cudaMemsetAsync(scr->err, 0, sizeof(scr->err), s));
+        MC_CUDA(cudaMemcpyAsync(scr->sigma, cc->sigma_i.data(), (size_t)ncls * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, s));
+        SampleArgs a;
+        fill_sample_args(a, t, h);
+        const ShapeCatalog &cat = shape_catalog();
+        a.allow0 = a.allow1 = 0;
+        for (int i = 0; i < cat.r[h]; ++i) {
+            if (i < 64) a.allow0 |= 1ull << i; else a.allow1 |= 1ull << (i - 64);
+        }
+        a.prefix = t->prefix[h];
+        a.R = t->R[h];
+        a.seed = seed;
+        a.first_index = first_index;
+        a.count = samples;
+        a.lut = cc->lut;
+        a.hist = scr->hist;
+        a.ncls = ncls;
+        a.err = scr->err;
+        launch_sampler(t, a, s);
+        const double ip = inv_colourful_prob(t->k, h);
+        MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(
+                                     scr->hist, scr->sigma, ncls, t->R[h] / (u128)h, samples, ip, scr->est));
+        int herr[2] = {0, 0};
+        MC_CUDA(cudaMemcpyAsync(hits, scr->hist, (size_t)ncls * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(est, scr->est, (size_t)ncls * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(herr, scr->err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
+    });
+}
