@@ -24,7 +24,7 @@ enum : int { ERR_OVERFLOW = 1, ERR_INEXACT = 2, ERR_COLOUR = 4, ERR_SEARCH = 8 }
 // ---------------------------------------------------------------------------
 template <typename CT>
 __global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict__ row_ptr,
-                                                      const uint32_t *__restrict__ col,
+                                                      const uint8_t *__restrict__ ecol,
                                                       const uint8_t *__restrict__ colors, int64_t n,
                                                       int k, CT *__restrict__ S1)
 {
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict_
         uint32_t cnt = 0;  // lane a (< k-1) counts relative colour a
         for (int64_t b = e0; b < e1; b += 32) {
             const int64_t e = b + lane;
-            const int cu = e < e1 ? (int)colors[col[e]] : -1;
+            const int cu = e < e1 ? (int)ecol[e] : -1;
             for (int a = 0; a < k - 1; ++a) {
                 const int abs_a = a < cv ? a : a + 1;
                 const unsigned m = __ballot_sync(0xffffffffu, cu == abs_a);
@@ -45,6 +45,41 @@ __global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict_
             }
         }
         if (lane < k - 1) S1[v * (k - 1) + lane] = (CT)cnt;
+    }
+}
+
+// Level-1 partial sums of each hub chunk (colour counts of its neighbours),
+// kept with the tables for the sampler's chunk skipping.
+template <typename CT>
+__global__ void __launch_bounds__(256) chunk1_kernel(const uint8_t *__restrict__ ecol,
+                                                     const uint8_t *__restrict__ colors,
+                                                     const uint32_t *__restrict__ chunk_node,
+                                                     const int64_t *__restrict__ chunk_e0,
+                                                     const int64_t *__restrict__ chunk_e1,
+                                                     const int32_t *__restrict__ node_chunk0,
+                                                     const int64_t *__restrict__ row_ptr, int64_t n_chunks,
+                                                     int k, CT *__restrict__ Sp1)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < n_chunks; c += nwarps) {
+        const uint32_t v = chunk_node[c];
+        const int cv = colors[v];
+        const int64_t e0 = chunk_e0[c], e1 = chunk_e1[c];
+        const int64_t c0 = node_chunk0[v];
+        const int64_t nch = (row_ptr[v + 1] - row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
+        uint32_t cnt = 0;
+        for (int64_t b = e0; b < e1; b += 32) {
+            const int64_t e = b + lane;
+            const int cu = e < e1 ? (int)ecol[e] : -1;
+            for (int a = 0; a < k - 1; ++a) {
+                const int abs_a = a < cv ? a : a + 1;
+                const unsigned m = __ballot_sync(0xffffffffu, cu == abs_a);
+                if (lane == a) cnt += __popc(m);
+            }
+        }
+        if (lane < k - 1) Sp1[c0 * (k - 1) + lane * nch + (c - c0)] = (CT)cnt;
     }
 }
 
@@ -60,6 +95,8 @@ struct GatherArgs {
     const int64_t *row_ptr;
     const uint32_t *col;
     const uint8_t *colors;
+    const uint8_t *ecol;
+    const int32_t *node_chunk0;
     const void *src;   // c_h, n x Wc
     void *dst;         // S_h, n x Ws
     void *partial;     // n_chunks x Ws
@@ -100,11 +137,16 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
     for (int64_t t = warp; t < ntasks; t += nwarps) {
         int64_t v, e0, e1;
         CT *out;
+        int64_t ostride = 1;
         if (t < a.n_chunks) {
+            // partial row of one hub chunk, stored entry-major per hub:
+            // [first chunk * Ws + entry * (chunks of the hub) + chunk]
             v = a.chunk_node[t];
             e0 = a.chunk_e0[t];
             e1 = a.chunk_e1[t];
-            out = (CT *)a.partial + t * a.Ws;
+            const int64_t c0 = a.node_chunk0[v];
+            ostride = (a.row_ptr[v + 1] - a.row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
+            out = (CT *)a.partial + c0 * a.Ws + (t - c0);
         } else {
             v = t - a.n_chunks;
             e0 = a.row_ptr[v];
@@ -117,9 +159,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 #pragma unroll
         for (int i = 0; i < MAXE; ++i) acc[i] = 0;
         for (int64_t e = e0 + grp; e < e1; e += NG) {
-            const uint32_t u = a.col[e];
-            const int cu = a.colors[u];
+            const int cu = a.ecol[e];
             if (cu == cv) continue;  // every set holding c_u also holds c_v
+            const uint32_t u = a.col[e];
             const CT *row = src + (int64_t)u * a.Wc;
             const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
 #pragma unroll
@@ -140,7 +182,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
         if (grp == 0) {
 #pragma unroll
             for (int i = 0; i < MAXE; ++i)
-                if (own[i]) out[j + i * G] = acc[i];
+                if (own[i]) out[(j + i * G) * ostride] = acc[i];
         }
     }
     if (ovf) atomicOr(a.err, ERR_OVERFLOW);
@@ -159,8 +201,10 @@ __global__ void hub_reduce_kernel(const CT *__restrict__ partial, CT *__restrict
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t hub = i / Ws;
         const int e = (int)(i - hub * Ws);
+        const int64_t c0 = hub_chunk0[hub], nch = hub_chunk0[hub + 1] - c0;
+        const CT *p = partial + c0 * Ws + e * nch;
         CT s = 0;
-        for (int64_t c = hub_chunk0[hub]; c < hub_chunk0[hub + 1]; ++c) ovf |= add_ovf(s, partial[c * Ws + e]);
+        for (int64_t c = 0; c < nch; ++c) ovf |= add_ovf(s, p[c]);
         dst[(int64_t)hub_node[hub] * Ws + e] = s;
     }
     if (ovf) atomicOr(err, ERR_OVERFLOW);
@@ -223,28 +267,33 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
 // prefix over the nodes (the cumulative counts of Section 3.2.1, taken over
 // nodes for the root draw).
 // ---------------------------------------------------------------------------
-template <typename CT>
+template <typename CT, int G>
 __global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ c, int64_t n, int W, int Bc,
                                                          uint64_t allow0, uint64_t allow1,
                                                          u128 *__restrict__ tot, int *err)
 {
+    // groups of G lanes per node, 32/G nodes per warp
     const int lane = threadIdx.x & 31;
+    const int grp = lane / G, j = lane % G;
+    constexpr int NG = 32 / G;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     bool ovf = false;
-    for (int64_t v = warp; v < n; v += nwarps) {
+    for (int64_t v0 = warp * NG; v0 < n; v0 += nwarps * NG) {
+        const int64_t v = v0 + grp;
         u128 s = 0;
-        for (int e = lane; e < W; e += 32) {
-            const int sh = e / Bc;
-            const bool ok = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
-            if (ok) ovf |= add_ovf(s, widen(c[v * W + e]));
-        }
+        if (v < n)
+            for (int e = j; e < W; e += G) {
+                const int sh = e / Bc;
+                const bool ok = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
+                if (ok) ovf |= add_ovf(s, widen(c[v * W + e]));
+            }
 #pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
+        for (int d = 1; d < G; d <<= 1) {
             const u128 o = shfl_xor(s, d);
             ovf |= add_ovf(s, o);
         }
-        if (lane == 0) tot[v] = s;
+        if (j == 0 && v < n) tot[v] = s;
     }
     if (ovf) atomicOr(err, ERR_OVERFLOW);
 }
@@ -328,6 +377,53 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_apply_kernel(u128 *__restri
     }
 }
 
+// Colour of every edge's far end, so that neighbour loops read colours
+// contiguously instead of one random byte per neighbour.
+__global__ void edge_colours_kernel(const uint32_t *__restrict__ col, const uint8_t *__restrict__ colors,
+                                    int64_t nnz, uint8_t *__restrict__ ecol)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x)
+        ecol[e] = colors[col[e]];
+}
+
+// Root-search buckets: X in [0, R) falls in bucket b = floor(X / D), D =
+// ceil(R / nb); start[b] is the first node whose inclusive prefix exceeds
+// b * D, so the node drawn for X lies in [start[b], start[b + 1]].
+__global__ void bucket_width_kernel(const u128 *prefix, int64_t n, int64_t nb, u128 *D)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const u128 R = n > 0 ? prefix[n - 1] : 0;
+        u128 d = R / (u128)nb + ((R % (u128)nb) != 0 ? 1 : 0);
+        *D = d ? d : 1;
+    }
+}
+
+__global__ void bucket_kernel(const u128 *__restrict__ prefix, int64_t n, int64_t nb, const u128 *Dp,
+                              uint32_t *__restrict__ start)
+{
+    const u128 D = *Dp;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= nb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const u128 X = (u128)b * D;
+        int64_t lo = 0, hi = n;  // first v with prefix[v] > X, else n - 1
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (prefix[mid] > X) hi = mid; else lo = mid + 1;
+        }
+        start[b] = (uint32_t)(lo < n ? lo : n - 1);
+    }
+}
+
+void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t *start, cudaStream_t s)
+{
+    if (n <= 0) return;
+    MC_LAUNCH("bucket_width", s, bucket_width_kernel<<<1, 32, 0, s>>>(prefix, n, nb, dD));
+    MC_LAUNCH("buckets", s, bucket_kernel<<<grid_for(nb + 1, 256), 256, 0, s>>>(prefix, n, nb, dD, start));
+}
+
+int64_t bucket_count(int64_t n) { return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)1 << 22)); }
+
 __global__ void check_colours_kernel(const uint8_t *colors, int64_t n, int k, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -378,17 +474,33 @@ ExactDiv make_div(int beta)
 
 template <typename CT> size_t bytes_of() { return sizeof(CT); }
 
+template <typename CT>
+static void launch_row_totals_t(const CT *c, int64_t n, int W, int Bc, uint64_t allow0, uint64_t allow1, u128 *tot,
+                                int *err, cudaStream_t s)
+{
+    int G = 1;
+    while (G < W && G < 32) G <<= 1;
+    const int grid = grid_for((n * G + 31) / 32 * 32, 256);
+    switch (G) {
+    case 1: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 1><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    case 2: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 2><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    case 4: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 4><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    case 8: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 8><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    case 16: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 16><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    default: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 32><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    }
+}
+
 void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
                        cudaStream_t s)
 {
     const int64_t n = t->g->n;
     if (n == 0) return;
     const int W = t->geo.Wc[h], Bc = t->geo.Bc[h];
-    const int grid = grid_for(n * 32, 256);
     if (t->bits == 64)
-        MC_LAUNCH("row_totals", s, row_totals_kernel<uint64_t><<<grid, 256, 0, s>>>((const uint64_t *)t->c[h], n, W, Bc, allow0, allow1, tot, err));
+        launch_row_totals_t<uint64_t>((const uint64_t *)t->c[h], n, W, Bc, allow0, allow1, tot, err, s);
     else
-        MC_LAUNCH("row_totals", s, row_totals_kernel<u128><<<grid, 256, 0, s>>>((const u128 *)t->c[h], n, W, Bc, allow0, allow1, tot, err));
+        launch_row_totals_t<u128>((const u128 *)t->c[h], n, W, Bc, allow0, allow1, tot, err, s);
 }
 
 static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gather_h2", "gather_h3",
@@ -421,10 +533,11 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
     const int64_t n = g->n;
     if (n == 0) return;
     // level 1 neighbour sums
-    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, g->col, t->colors, n, k, (CT *)t->S[1]));
-    int maxWs = 0;
-    for (int h = 2; h <= k - 1; ++h) maxWs = std::max(maxWs, G.Ws[h]);
-    CT *partial = g->n_chunks && maxWs ? scratch.get<CT>((size_t)g->n_chunks * maxWs) : nullptr;
+    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, t->ecol, t->colors, n, k, (CT *)t->S[1]));
+    if (g->n_chunks && k >= 2)
+        MC_LAUNCH("chunk_h1", s, chunk1_kernel<CT><<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
+                                     t->ecol, t->colors, g->chunk_node, g->chunk_e0, g->chunk_e1, g->node_chunk0,
+                                     g->row_ptr, g->n_chunks, k, (CT *)t->Sp[1]));
 
     MergeArgs ma{};
     for (int h = 1; h <= k; ++h) {
@@ -448,9 +561,11 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
             ga.row_ptr = g->row_ptr;
             ga.col = g->col;
             ga.colors = t->colors;
+            ga.ecol = t->ecol;
+            ga.node_chunk0 = g->node_chunk0;
             ga.src = t->c[h];
             ga.dst = t->S[h];
-            ga.partial = partial;
+            ga.partial = t->Sp[h];
             ga.chunk_node = g->chunk_node;
             ga.chunk_e0 = g->chunk_e0;
             ga.chunk_e1 = g->chunk_e1;
@@ -468,7 +583,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
             launch_gather<CT>(ga, grp, h, s);
             if (g->n_hubs) {
                 MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
-                    partial, (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
+                    (const CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
             }
         }
     }
@@ -511,6 +626,11 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
             MC_CUDA(cudaMemcpyAsync(t->colors, colors, (size_t)n, cudaMemcpyDefault, s));
             MC_LAUNCH("check_colours", s, check_colours_kernel<<<grid_for(n, 256), 256, 0, s>>>(t->colors, n, k, err));
         }
+        t->ecol = t->arena.get<uint8_t>((size_t)g->nnz);
+        if (g->nnz) {
+            MC_LAUNCH("edge_colours", s, edge_colours_kernel<<<grid_for(g->nnz, 256), 256, 0, s>>>(
+                                             g->col, t->colors, g->nnz, t->ecol));
+        }
         // programs
         const Programs &P = programs(k);
         for (int h = 2; h <= k; ++h) {
@@ -530,18 +650,26 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         // tables
         for (int h = 2; h <= k; ++h) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
         for (int h = 1; h <= k - 1; ++h) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
+        for (int h = 1; h <= k - 1; ++h) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
         for (int h = 2; h <= k; ++h) t->prefix[h] = t->arena.get<u128>((size_t)n);
         if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
         else build_levels<u128>(t, err, scratch, s);
         // node prefixes of the level totals, for the root draw
+        t->nbucket = bucket_count(n);
+        u128 *dD = scratch.get<u128>(MAXK + 1);
         for (int h = 2; h <= k; ++h) {
             launch_row_totals(t, h, ~0ull, ~0ull, t->prefix[h], err, s);
             inclusive_scan_u128(t->prefix[h], n, err, scratch, s);
+            t->bucket[h] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
+            build_buckets(t->prefix[h], n, t->nbucket, dD + h, t->bucket[h], s);
         }
         int herr = 0;
         MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         for (int h = 2; h <= k; ++h)
-            if (n) MC_CUDA(cudaMemcpyAsync(&t->R[h], t->prefix[h] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            if (n) {
+                MC_CUDA(cudaMemcpyAsync(&t->R[h], t->prefix[h] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaMemcpyAsync(&t->bucketD[h], dD + h, sizeof(u128), cudaMemcpyDeviceToHost, s));
+            }
         MC_CUDA(cudaStreamSynchronize(s));
         if (herr & ERR_COLOUR) throw Error(MC_E_INVALID, "a colour is >= k");
         if (herr & ERR_OVERFLOW)

@@ -171,6 +171,23 @@ __device__ __forceinline__ bool draw_below(uint64_t seed, uint64_t index, uint32
     return false;
 }
 
+// The same draw when W < 2^64: the mask keeps only the low 64 of the 128
+// Philox bits, so the value is identical to the 128-bit draw above.
+__device__ __forceinline__ bool draw_below(uint64_t seed, uint64_t index, uint32_t step, uint64_t W, uint64_t &out)
+{
+    if (W == 0) return false;
+    const uint64_t wm1 = W - 1;
+    const int bits = 64 - __clzll(wm1);
+    const uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+    for (uint32_t attempt = 0; attempt < 128; ++attempt) {
+        uint32_t c[4] = {(uint32_t)index, (uint32_t)(index >> 32), step, attempt};
+        philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t r = ((uint64_t)c[0] | ((uint64_t)c[1] << 32)) & mask;
+        if (r < W) { out = r; return true; }
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // Colour sets.  A set of colours is a bit mask (bit a = colour a).  Tables
 // are colour-relative: at node v the colour c_v is deleted from the palette

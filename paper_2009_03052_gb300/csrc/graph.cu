@@ -297,6 +297,11 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
             }
         }
         h0.push_back((int64_t)cn.size());
+        MC_REQUIRE(cn.size() < (size_t)0x7fffffff, "too many hub chunks");
+        std::vector<int32_t> nc0((size_t)n, -1);
+        for (size_t i = 0; i < hn.size(); ++i) nc0[hn[i]] = (int32_t)h0[i];
+        g->node_chunk0 = g->arena.get<int32_t>((size_t)n);
+        if (n) MC_CUDA(cudaMemcpyAsync(g->node_chunk0, nc0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
         g->n_hubs = (int64_t)hn.size();
         g->n_chunks = (int64_t)cn.size();
         g->chunk_node = g->arena.get<uint32_t>(cn.size());

@@ -105,7 +105,7 @@ void prof_end(ProfSpan &span, cudaStream_t s);
 // Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
 // partial sums are added afterwards.
-constexpr int HUB_CHUNK = 256;
+constexpr int HUB_CHUNK = 64;
 
 }  // namespace mc
 
@@ -119,6 +119,7 @@ struct mc_graph {
     int64_t *chunk_e0 = nullptr, *chunk_e1 = nullptr;
     uint32_t *hub_node = nullptr;
     int64_t *hub_chunk0 = nullptr;  // n_hubs + 1 entries
+    int32_t *node_chunk0 = nullptr; // per node: its first chunk if it is a hub, else -1
     mc::Arena arena;
 };
 
@@ -127,10 +128,15 @@ struct mc_tables {
     int k = 0, bits = 64;
     mc::Geometry geo;
     uint8_t *colors = nullptr;                 // device uint8[n]
+    uint8_t *ecol = nullptr;                   // device uint8[nnz]: colour of col[e]
     void *c[mc::MAXK + 1] = {nullptr};         // level h >= 2: n x Wc[h] counts
     void *S[mc::MAXK + 1] = {nullptr};         // level h <= k-1: n x Ws[h] counts
+    void *Sp[mc::MAXK + 1] = {nullptr};        // level h <= k-1: hub chunk partial sums, n_chunks x Ws[h]
     mc::u128 *prefix[mc::MAXK + 1] = {nullptr};  // inclusive node prefix of level totals
     mc::u128 R[mc::MAXK + 1] = {0};            // rooted totals
+    uint32_t *bucket[mc::MAXK + 1] = {nullptr}; // root-search buckets over [0, R) (see sample.cu)
+    mc::u128 bucketD[mc::MAXK + 1] = {0};
+    int64_t nbucket = 0;
     // merge and gather programs (device)
     int32_t *m_info[mc::MAXK + 1] = {nullptr};
     int32_t *m_off[mc::MAXK + 1] = {nullptr};

@@ -11,8 +11,6 @@
 
 namespace mc {
 
-void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
-                       cudaStream_t s);
 void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s);
 
 enum : int { SERR_SEARCH = 1, SERR_CLASS = 2 };
@@ -296,17 +294,23 @@ struct SampleArgs {
     const int64_t *row_ptr;
     const uint32_t *col;
     const uint8_t *colors;
+    const uint8_t *ecol;
     int64_t n;
     const void *c[MAXK + 1];
     const void *S[MAXK + 1];
+    const void *Sp[MAXK + 1];   // hub chunk partial sums per level
+    const int32_t *node_chunk0; // first chunk of a hub, -1 for other nodes
     int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
     int k, h;
     const u128 *prefix;
     u128 R;
+    const uint32_t *bucket;     // root-search buckets (nb + 1 entries)
+    u128 D;                     // bucket width
     uint64_t allow0, allow1;
     int first[MAXK + 2];
     uint8_t sz[MAX_SHAPES], loc[MAX_SHAPES], lft[MAX_SHAPES], rgt[MAX_SHAPES], beta[MAX_SHAPES];
-    uint8_t crank[1 << (MAXK - 1)];
+    uint8_t crank[1 << (MAXK - 1)];        // colex rank of a set of the k-1 relative colours
+    uint8_t unrank[MAXK][36];              // i-th m-subset (ascending masks)
     uint8_t pi[28], pj[28];
     uint64_t seed, first_index;
     int64_t count;
@@ -318,17 +322,29 @@ struct SampleArgs {
     int *err;
 };
 
-template <typename CT>
-__device__ __forceinline__ u128 count_at(const SampleArgs &a, int g, unsigned C, uint32_t x, int cx)
+struct SampleSmem {
+    uint8_t crank[1 << (MAXK - 1)];
+    uint8_t unrank[MAXK][36];
+};
+
+template <typename CT, typename V>
+__device__ __forceinline__ V count_at(const SampleArgs &a, const SampleSmem &sm, int g, unsigned C, uint32_t x, int cx)
 {
     const int hg = a.sz[g];
     if (hg == 1) return 1;
     const unsigned rel = drop_colour(C & ~(1u << cx), cx);
     const CT *row = (const CT *)a.c[hg] + (int64_t)x * a.Wc[hg];
-    return widen(row[a.loc[g] * a.Bc[hg] + a.crank[rel]]);
+    return (V)row[a.loc[g] * a.Bc[hg] + sm.crank[rel]];
 }
 
-// k-th set bit (0-based) positions of `rest` selected by index mask `im`
+__device__ __forceinline__ uint64_t quotient(uint64_t a, uint64_t b) { return a / b; }
+__device__ __forceinline__ u128 quotient(u128 a, u128 b)
+{
+    return ((a >> 64) == 0 && (b >> 64) == 0) ? (u128)((uint64_t)a / (uint64_t)b) : a / b;
+}
+
+// the set bits of `rest` selected by index mask `im` (i-th bit of im picks
+// the i-th lowest set bit of rest)
 __device__ __forceinline__ unsigned deposit(unsigned im, unsigned rest)
 {
     unsigned out = 0;
@@ -338,14 +354,6 @@ __device__ __forceinline__ unsigned deposit(unsigned im, unsigned rest)
         rest &= rest - 1;
     }
     return out;
-}
-
-// i-th (0-based) index mask of popcount m over nb bits in ascending order
-__device__ __forceinline__ unsigned nth_subset(int nb, int m, int i)
-{
-    for (unsigned x = 0; x < (1u << nb); ++x)
-        if (__popc(x) == m && i-- == 0) return x;
-    return 0;
 }
 
 __device__ __forceinline__ bool adjacent(const int64_t *row_ptr, const uint32_t *col, uint32_t a, uint32_t b)
@@ -361,14 +369,80 @@ __device__ __forceinline__ bool adjacent(const int64_t *row_ptr, const uint32_t 
     return lo < end && col[lo] == b;
 }
 
-template <typename CT>
-__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleArgs a)
+__device__ __forceinline__ uint64_t warp_inclusive_scan(uint64_t x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+__device__ __forceinline__ uint64_t shfl(uint64_t x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+
+// Over items i = 0 .. len-1 in order, the first whose running sum of val(i)
+// exceeds q (-1 if none); `before` receives the running sum before it.  Up
+// to 32*IPL items per pass: lane l takes ceil(n/32) consecutive items, so
+// their loads are independent; a warp scan of the lane totals finds the
+// lane, the lane finds the item.  Exact integers: the result is that of a
+// flat scan in order.
+template <int IPL, typename V, typename F>
+__device__ __forceinline__ int64_t warp_first_exceeding(int64_t len, V q, F val, V &before)
+{
+    const int lane = threadIdx.x & 31;
+    V run = 0;
+    for (int64_t b = 0; b < len; b += 32 * IPL) {
+        const int64_t n = len - b < 32 * IPL ? len - b : 32 * IPL;
+        const int ipl = (int)((n + 31) >> 5);
+        const int64_t mine = b + (int64_t)lane * ipl;
+        V v[IPL];
+        V tot = 0;
+#pragma unroll
+        for (int i = 0; i < IPL; ++i) {
+            v[i] = 0;
+            if (i < ipl && mine + i < b + n) v[i] = val(mine + i);
+            tot += v[i];
+        }
+        const V incl = warp_inclusive_scan(tot);
+        const unsigned m = __ballot_sync(0xffffffffu, run + incl > q);
+        if (m) {
+            const int f = __ffs(m) - 1;
+            int64_t sel = -1;
+            V bf = 0;
+            if (lane == f) {
+                V c = run + incl - tot;
+                bool done = false;
+#pragma unroll
+                for (int i = 0; i < IPL; ++i) {
+                    if (!done && i < ipl) {
+                        if (c + v[i] > q) { sel = mine + i; bf = c; done = true; }
+                        else c += v[i];
+                    }
+                }
+            }
+            sel = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)sel, f);
+            before = shfl(bf, f);
+            return sel;
+        }
+        run += shfl(incl, 31);
+    }
+    return -1;
+}
+
+// CT: the count type of the tables; V: the type of the descent's weights,
+// draws and running sums (64 bits when every level total fits with room for
+// beta, else 128 bits).
+template <typename CT, typename V>
+__global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ SampleArgs a)
 {
     extern __shared__ unsigned int s_hist[];
-    if (a.hist) {
+    __shared__ SampleSmem sm;
+    for (int i = threadIdx.x; i < (1 << (MAXK - 1)); i += blockDim.x) sm.crank[i] = a.crank[i];
+    for (int i = threadIdx.x; i < MAXK * 36; i += blockDim.x) (&sm.unrank[0][0])[i] = (&a.unrank[0][0])[i];
+    if (a.hist)
         for (int i = threadIdx.x; i < a.ncls; i += blockDim.x) s_hist[i] = 0;
-        __syncthreads();
-    }
+    __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -377,15 +451,17 @@ __global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ Sam
     bool bad = false;
     for (int64_t sid = warp; sid < a.count; sid += nwarps) {
         const uint64_t index = a.first_index + (uint64_t)sid;
-        // ---- root node
-        u128 X;
-        if (!draw_below(a.seed, index, 0, a.R, X)) { bad = true; continue; }
-        int64_t lo = 0, hi = a.n;
+        // ---- root node: first v with prefix[v] > X; the bucket of X bounds
+        // the range, a 32-ary warp search finishes it
+        V X;
+        if (!draw_below(a.seed, index, 0, (V)a.R, X)) { bad = true; continue; }
+        const uint64_t bk = (uint64_t)(X / (V)a.D);
+        int64_t lo = a.bucket[bk], hi = (int64_t)a.bucket[bk + 1] + 1;
         while (hi - lo > 32) {
             const int64_t step = (hi - lo + 31) >> 5;
             int64_t probe = lo + (lane + 1) * step - 1;
             if (probe > hi - 1) probe = hi - 1;
-            const unsigned m = __ballot_sync(FULL, a.prefix[probe] > X);
+            const unsigned m = __ballot_sync(FULL, a.prefix[probe] > (u128)X);
             const int f = m ? __ffs(m) - 1 : 31;
             const int64_t nlo = lo + f * step;
             const int64_t nhi = min(hi, lo + (f + 1) * step);
@@ -393,118 +469,102 @@ __global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ Sam
             hi = nhi;
         }
         const int64_t cand = lo + lane;
-        const unsigned mv = __ballot_sync(FULL, cand < hi && a.prefix[cand] > X);
+        const unsigned mv = __ballot_sync(FULL, cand < hi && a.prefix[cand] > (u128)X);
         if (!mv) { bad = true; continue; }
         const uint32_t v = (uint32_t)(lo + __ffs(mv) - 1);
-        const u128 rem = X - (v ? a.prefix[v - 1] : (u128)0);
-        // ---- entry of v's level-h row
+        const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
+        // ---- entry of v's level-h row, in (shape id, colour mask) order
         const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
-        int found = -1;
-        {
-            u128 run = 0;
-            for (int b = 0; b < a.Wc[h]; b += 32) {
-                const int e = b + lane;
-                u128 val = 0;
-                if (e < a.Wc[h]) {
-                    const int sh = e / a.Bc[h];
-                    const bool ok = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
-                    if (ok) val = widen(vrow[e]);
-                }
-                const u128 cum = warp_inclusive_scan(val) + run;
-                const unsigned m = __ballot_sync(FULL, cum > rem);
-                if (m) { found = b + __ffs(m) - 1; break; }
-                run = shfl(cum, 31);
-            }
-        }
+        V bfr;
+        const int found = (int)warp_first_exceeding<4, V>(a.Wc[h], rem, [&](int64_t e) -> V {
+            const int sh = (int)e / a.Bc[h];
+            const bool ok = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
+            return ok ? (V)vrow[e] : (V)0;
+        }, bfr);
         if (found < 0) { bad = true; continue; }
         const int cv0 = a.colors[v];
         const int s0 = found / a.Bc[h];
-        const unsigned C0 = (1u << cv0) | insert_colour_gap(nth_subset(a.k - 1, h - 1, found % a.Bc[h]), cv0);
-        // ---- descent
-        int stg[MAXK], sp = 0, nn = 0;
+        const unsigned C0 = (1u << cv0) | insert_colour_gap(sm.unrank[h - 1][found % a.Bc[h]], cv0);
+        // ---- descent over the decomposition, pre-order; each stack entry
+        // carries its node's colour
+        int stg[MAXK], stc[MAXK], sp = 0, nn = 0;
         unsigned stC[MAXK];
         uint32_t stx[MAXK], nodes[MAXK];
-        stg[0] = a.first[h] + s0; stC[0] = C0; stx[0] = v; sp = 1;
+        stg[0] = a.first[h] + s0; stC[0] = C0; stx[0] = v; stc[0] = cv0; sp = 1;
         uint32_t step = 0;
         while (sp > 0) {
             --sp;
             const int g = stg[sp];
             const unsigned C = stC[sp];
             const uint32_t x = stx[sp];
+            const int cx = stc[sp];
             if (a.sz[g] == 1) {
                 if (nn >= MAXK) { bad = true; break; }
                 nodes[nn++] = x;
                 continue;
             }
             ++step;
-            const int cx = a.colors[x];
             const int ga = a.lft[g], gb = a.rgt[g];
             const int hb = a.sz[gb];
-            const u128 W = (u128)a.beta[g] * count_at<CT>(a, g, C, x, cx);
-            u128 Y;
+            const int64_t e0 = a.row_ptr[x], e1 = a.row_ptr[x + 1];
+            const int chunk0 = a.node_chunk0[x];
+            const V W = (V)a.beta[g] * count_at<CT, V>(a, sm, g, C, x, cx);
+            V Y;
             if (!draw_below(a.seed, index, step, W, Y)) { bad = true; break; }
             const unsigned rest = C & ~(1u << cx);
             const int nr = __popc(rest);
-            const int nsub = [&] { int r = 1; for (int i = 1; i <= hb; ++i) r = r * (nr - hb + i) / i; return r; }();
-            // block of C''
-            int blk = -1;
-            u128 before = 0, run = 0;
-            unsigned C2 = 0;
-            for (int b = 0; b < nsub; b += 32) {
-                const int i = b + lane;
-                u128 wgt = 0;
-                unsigned c2 = 0;
-                if (i < nsub) {
-                    c2 = deposit(nth_subset(nr, hb, i), rest);
-                    const u128 x1 = count_at<CT>(a, ga, C & ~c2, x, cx);
-                    const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
-                    wgt = x1 * widen(srow[a.loc[gb] * a.Bs[hb] + a.crank[drop_colour(c2, cx)]]);
-                }
-                const u128 cum = warp_inclusive_scan(wgt) + run;
-                const unsigned m = __ballot_sync(FULL, cum > Y);
-                if (m) {
-                    const int f = __ffs(m) - 1;
-                    blk = b + f;
-                    before = shfl(cum, f) - shfl(wgt, f);
-                    C2 = __shfl_sync(FULL, c2, f);
-                    break;
-                }
-                run = shfl(cum, 31);
-            }
+            int nsub = 1;
+            for (int i = 1; i <= hb; ++i) nsub = nsub * (nr - hb + i) / i;
+            // block of C'' (ascending mask): weights c(T'_{C \ C''}, x) S(T'', C'', x)
+            const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
+            const int sbase = a.loc[gb] * a.Bs[hb];
+            V before;
+            const int blk = (int)warp_first_exceeding<2, V>(nsub, Y, [&](int64_t i) -> V {
+                const unsigned c2 = deposit(sm.unrank[hb][i], rest);
+                return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) * (V)srow[sbase + sm.crank[drop_colour(c2, cx)]];
+            }, before);
             if (blk < 0) { bad = true; break; }
+            const unsigned C2 = deposit(sm.unrank[hb][blk], rest);
             const unsigned C1 = C & ~C2;
-            const u128 x1 = count_at<CT>(a, ga, C1, x, cx);
-            const u128 Yp = Y - before;
-            const u128 q = ((Yp >> 64) == 0 && (x1 >> 64) == 0) ? (u128)((uint64_t)Yp / (uint64_t)x1) : Yp / x1;
-            // neighbour
-            const int64_t e0 = a.row_ptr[x], e1 = a.row_ptr[x + 1];
-            int64_t sel = -1;
-            run = 0;
-            const int lb = a.loc[gb];
-            for (int64_t b = e0; b < e1; b += 32) {
-                const int64_t e = b + lane;
-                u128 val = 0;
-                if (e < e1) {
-                    const uint32_t u = a.col[e];
-                    const int cu = a.colors[u];
-                    if ((C2 >> cu) & 1u) {
-                        if (hb == 1) val = 1;
-                        else {
-                            const CT *urow = (const CT *)a.c[hb] + (int64_t)u * a.Wc[hb];
-                            val = widen(urow[lb * a.Bc[hb] + a.crank[drop_colour(C2 & ~(1u << cu), cu)]]);
-                        }
-                    }
-                }
-                const u128 cum = warp_inclusive_scan(val) + run;
-                const unsigned m = __ballot_sync(FULL, cum > q);
-                if (m) { sel = b + __ffs(m) - 1; break; }
-                run = shfl(cum, 31);
+            const V x1 = count_at<CT, V>(a, sm, ga, C1, x, cx);
+            const V Yp = Y - before;
+            const CT q = (CT)quotient(Yp, x1);  // q < S(T'', C'', x), which fits the count type
+            // neighbour: first u (ascending) whose running sum of c(T''_{C''}, u)
+            // exceeds q; at a hub, first its 256-neighbour chunk from the
+            // chunk partial sums, then inside that chunk
+            int64_t lo_e = e0, hi_e = e1;
+            CT qq = q;
+            const int sidx = sbase + sm.crank[drop_colour(C2, cx)];
+            if (chunk0 >= 0) {
+                const int64_t nch = (e1 - e0 + HUB_CHUNK - 1) / HUB_CHUNK;
+                // this hub's partial sums of entry sidx, one per chunk, contiguous
+                const CT *spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
+                CT bc;
+                const int64_t ci = warp_first_exceeding<4, CT>(nch, q, [&](int64_t i) -> CT {
+                    return spp[i];
+                }, bc);
+                if (ci < 0) { bad = true; break; }
+                lo_e = e0 + ci * HUB_CHUNK;
+                hi_e = min(e1, lo_e + HUB_CHUNK);
+                qq = q - bc;
             }
+            const int lb = a.loc[gb];
+            const CT *chb = (const CT *)a.c[hb];
+            const int bcb = a.Bc[hb], wcb = a.Wc[hb];
+            CT bn;
+            const int64_t sel = warp_first_exceeding<(HUB_CHUNK + 31) / 32, CT>(hi_e - lo_e, qq, [&](int64_t i) -> CT {
+                const int cu = a.ecol[lo_e + i];
+                if (!((C2 >> cu) & 1u)) return (CT)0;
+                if (hb == 1) return (CT)1;
+                const uint32_t u = a.col[lo_e + i];
+                return chb[(int64_t)u * wcb + lb * bcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)]];
+            }, bn);
             if (sel < 0) { bad = true; break; }
-            const uint32_t u = a.col[sel];
+            const uint32_t u = a.col[lo_e + sel];
+            const int cu = a.ecol[lo_e + sel];
             if (sp + 2 > MAXK) { bad = true; break; }
-            stg[sp] = gb; stC[sp] = C2; stx[sp] = u; ++sp;
-            stg[sp] = ga; stC[sp] = C1; stx[sp] = x; ++sp;
+            stg[sp] = gb; stC[sp] = C2; stx[sp] = u; stc[sp] = cu; ++sp;
+            stg[sp] = ga; stC[sp] = C1; stx[sp] = x; stc[sp] = cx; ++sp;
         }
         if (nn != h) { bad = true; continue; }
         for (int i = 1; i < h; ++i)
@@ -559,10 +619,13 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
     a.row_ptr = g->row_ptr;
     a.col = g->col;
     a.colors = t->colors;
+    a.ecol = t->ecol;
     a.n = g->n;
+    a.node_chunk0 = g->node_chunk0;
     for (int i = 1; i <= t->k; ++i) {
         a.c[i] = t->c[i];
         a.S[i] = t->S[i];
+        a.Sp[i] = t->Sp[i];
         a.Bc[i] = t->geo.Bc[i];
         a.Bs[i] = t->geo.Bs[i];
         a.Wc[i] = t->geo.Wc[i];
@@ -580,6 +643,8 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
         a.beta[gid] = (uint8_t)s.beta;
     }
     for (unsigned m = 0; m < (1u << (t->k - 1)); ++m) a.crank[m] = (uint8_t)colex_rank(m);
+    for (int m = 0; m < MAXK; ++m)
+        for (int i = 0; i < binom(MAXK - 1, m); ++i) a.unrank[m][i] = (uint8_t)colex_unrank(m, i);
     int p = 0;
     for (int i = 0; i < h; ++i)
         for (int j = i + 1; j < h; ++j) { a.pi[p] = (uint8_t)i; a.pj[p] = (uint8_t)j; ++p; }
@@ -588,7 +653,13 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
 struct RootIndex {
     const u128 *prefix = nullptr;
     u128 R = 0;
+    const uint32_t *bucket = nullptr;
+    u128 D = 1;
 };
+
+void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
+                       cudaStream_t s);
+void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t *start, cudaStream_t s);
 
 static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scratch, int *err, cudaStream_t s,
                             uint64_t &allow0, uint64_t &allow1)
@@ -603,34 +674,49 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
     if (unrooted < 0) {
         ri.prefix = t->prefix[h];
         ri.R = t->R[h];
+        ri.bucket = t->bucket[h];
+        ri.D = t->bucketD[h];
         return ri;
     }
-    u128 *p = scratch.get<u128>((size_t)t->g->n);
+    const int64_t n = t->g->n;
+    u128 *p = scratch.get<u128>((size_t)n);
+    uint32_t *bk = scratch.get<uint32_t>((size_t)t->nbucket + 1);
+    u128 *dD = scratch.get<u128>(1);
     launch_row_totals(t, h, allow0, allow1, p, err, s);
-    inclusive_scan_u128(p, t->g->n, err, scratch, s);
-    MC_CUDA(cudaMemcpyAsync(&ri.R, p + (t->g->n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    inclusive_scan_u128(p, n, err, scratch, s);
+    build_buckets(p, n, t->nbucket, dD, bk, s);
+    if (n) {
+        MC_CUDA(cudaMemcpyAsync(&ri.R, p + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(&ri.D, dD, sizeof(u128), cudaMemcpyDeviceToHost, s));
+    }
     MC_CUDA(cudaStreamSynchronize(s));
     ri.prefix = p;
+    ri.bucket = bk;
     return ri;
 }
 
 static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
 {
     const int block = 256;
+    const size_t smem = a.hist ? (size_t)a.ncls * sizeof(unsigned int) : 0;
+    // one wave of resident blocks: the grid-stride loop then keeps every
+    // warp busy until the samples run out
+    // 64-bit descent arithmetic is exact when 8 R < 2^64: every weight is at
+    // most beta (<= 7) times a count of the level, every running sum at most
+    // a level total
+    const bool narrow = t->bits == 64 && (a.R >> 61) == 0;
+    auto kern = t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t> : sample_kernel<uint64_t, u128>)
+                              : sample_kernel<u128, u128>;
+    int per_sm = 0;
+    MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+    if (per_sm < 1) per_sm = 1;
     int64_t grid = (a.count * 32 + block - 1) / block;
-    const int64_t cap = (int64_t)sm_count() * 8;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    const size_t smem = a.hist ? (size_t)a.ncls * sizeof(unsigned int) : 0;
-    if (t->bits == 64) {
-        if (smem > 48 * 1024)
-            MC_CUDA(cudaFuncSetAttribute(sample_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MC_LAUNCH("sample", s, sample_kernel<uint64_t><<<(unsigned)grid, block, smem, s>>>(a));
-    } else {
-        if (smem > 48 * 1024)
-            MC_CUDA(cudaFuncSetAttribute(sample_kernel<u128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MC_LAUNCH("sample", s, sample_kernel<u128><<<(unsigned)grid, block, smem, s>>>(a));
-    }
+    if (smem > 48 * 1024)
+        MC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MC_LAUNCH("sample", s, kern<<<(unsigned)grid, block, smem, s>>>(a));
 }
 
 static double inv_colourful_prob(int k, int h)
@@ -723,6 +809,8 @@ extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape
         if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of the requested size/shape");
         a.prefix = ri.prefix;
         a.R = ri.R;
+        a.bucket = ri.bucket;
+        a.D = ri.D;
         a.seed = seed;
         a.first_index = first_index;
         a.count = count;
@@ -775,6 +863,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
             a.prefix = ri.prefix;
             a.R = ri.R;
+            a.bucket = ri.bucket;
+            a.D = ri.D;
             a.seed = p->seed;
             a.first_index = p->first_index;
             a.count = p->samples;
@@ -848,6 +938,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.allow1 = allows[cur].second;
                 a.prefix = ris[cur].prefix;
                 a.R = ris[cur].R;
+                a.bucket = ris[cur].bucket;
+                a.D = ris[cur].D;
                 a.seed = p->seed;
                 a.first_index = p->first_index + (uint64_t)drawn;
                 a.count = b;
@@ -989,6 +1081,8 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         }
         a.prefix = t->prefix[h];
         a.R = t->R[h];
+        a.bucket = t->bucket[h];
+        a.D = t->bucketD[h];
         a.seed = seed;
         a.first_index = first_index;
         a.count = samples;
