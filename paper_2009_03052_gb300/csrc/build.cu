@@ -158,17 +158,36 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
         CT acc[MAXE];
 #pragma unroll
         for (int i = 0; i < MAXE; ++i) acc[i] = 0;
-        for (int64_t e = e0 + grp; e < e1; e += NG) {
-            const int cu = a.ecol[e];
-            if (cu == cv) continue;  // every set holding c_u also holds c_v
-            const uint32_t u = a.col[e];
-            const CT *row = src + (int64_t)u * a.Wc;
-            const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
+        // 32 neighbours at a time: one coalesced load of their ids and
+        // colours, handed to the groups by shuffles; each group takes U of
+        // them per round so that U rows are in flight at once
+        constexpr int U = G < 4 ? G : 4;
+        for (int64_t b = e0; b < e1; b += 32) {
+            const int64_t e = b + lane;
+            const bool in = e < e1;
+            const uint32_t my_u = in ? a.col[e] : 0u;
+            const int my_cu = in ? (int)a.ecol[e] : cv;
+            const int nb = (int)min((int64_t)32, e1 - b);
+            const int rounds = (nb + NG * U - 1) / (NG * U);
+            for (int r = 0; r < rounds; ++r) {
 #pragma unroll
-            for (int i = 0; i < MAXE; ++i) {
-                if (own[i]) {
-                    const int sidx = gm[rho[i]];
-                    if (sidx >= 0) ovf |= add_ovf(acc[i], row[rowoff[i] + sidx]);
+                for (int uu = 0; uu < U; ++uu) {
+                    const int idx = r * NG * U + uu * NG + grp;
+                    const uint32_t u = __shfl_sync(0xffffffffu, my_u, idx & 31);
+                    const int cu = __shfl_sync(0xffffffffu, my_cu, idx & 31);
+                    // a neighbour of colour c_v adds nothing: every set holding
+                    // c_u then holds c_v
+                    if (idx < nb && cu != cv) {
+                        const CT *row = src + (int64_t)u * a.Wc;
+                        const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
+#pragma unroll
+                        for (int i = 0; i < MAXE; ++i) {
+                            if (own[i]) {
+                                const int sidx = gm[rho[i]];
+                                if (sidx >= 0) ovf |= add_ovf(acc[i], row[rowoff[i] + sidx]);
+                            }
+                        }
+                    }
                 }
             }
         }

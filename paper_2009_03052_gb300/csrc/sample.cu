@@ -430,11 +430,75 @@ __device__ __forceinline__ int64_t warp_first_exceeding(int64_t len, V q, F val,
     return -1;
 }
 
-// CT: the count type of the tables; V: the type of the descent's weights,
-// draws and running sums (64 bits when every level total fits with room for
-// beta, else 128 bits).
+// Per-lane search: over items 0 .. len-1 in order, the first whose running
+// sum of val(i) exceeds q (-1 if none), `before` the running sum before it.
+// Items are loaded four at a time so that their loads are in flight
+// together.
+template <typename V, typename F>
+__device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &before)
+{
+    V run = 0;
+    for (int b = 0; b < len; b += 4) {
+        V v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = b + i < len ? val(b + i) : (V)0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (b + i < len && run + v[i] > q) { before = run; return b + i; }
+            run += v[i];
+        }
+    }
+    return -1;
+}
+
+// Up to four adjacency tests at once (binary search of the shorter list),
+// advancing all searches one level per round so their loads overlap.
+__device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t *col, const uint32_t *qa,
+                                          const uint32_t *qb, int nq, bool *out)
+{
+    int64_t lo[4], hi[4], end[4];
+    uint32_t key[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i < nq) {
+            uint32_t x = qa[i], y = qb[i];
+            const int64_t dx = row_ptr[x + 1] - row_ptr[x], dy = row_ptr[y + 1] - row_ptr[y];
+            if (dy < dx) { const uint32_t t = x; x = y; y = t; }
+            lo[i] = row_ptr[x];
+            hi[i] = row_ptr[x + 1];
+            end[i] = hi[i];
+            key[i] = y;
+        } else {
+            lo[i] = hi[i] = end[i] = 0;
+            key[i] = 0;
+        }
+    }
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (lo[i] < hi[i]) {
+                const int64_t mid = (lo[i] + hi[i]) >> 1;
+                if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
+                more |= lo[i] < hi[i];
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = i < nq && lo[i] < end[i] && col[lo[i]] == key[i];
+}
+
+// Lane-per-sample sampler: the 32 lanes of a warp draw 32 samples and walk
+// their h-1 decomposition steps in lockstep (every h-treelet has h-1 internal
+// decomposition nodes).  A lane does its own scalar work and short scans; a
+// hub's chunk search longer than SEQ_CHUNKS is done by the whole warp, one
+// lane's search after another.  CT: the tables' count type; V: the type of
+// the descent's weights, draws and running sums (64 bits when every level
+// total leaves room for beta, else 128 bits).
+constexpr int SEQ_CHUNKS = 16;
+
 template <typename CT, typename V>
-__global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ SampleArgs a)
+__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleArgs a)
 {
     extern __shared__ unsigned int s_hist[];
     __shared__ SampleSmem sm;
@@ -449,143 +513,225 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int h = a.h;
     bool bad = false;
-    for (int64_t sid = warp; sid < a.count; sid += nwarps) {
+    for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
+        const int64_t sid = base + lane;
         const uint64_t index = a.first_index + (uint64_t)sid;
-        // ---- root node: first v with prefix[v] > X; the bucket of X bounds
-        // the range, a 32-ary warp search finishes it
-        V X;
-        if (!draw_below(a.seed, index, 0, (V)a.R, X)) { bad = true; continue; }
-        const uint64_t bk = (uint64_t)(X / (V)a.D);
-        int64_t lo = a.bucket[bk], hi = (int64_t)a.bucket[bk + 1] + 1;
-        while (hi - lo > 32) {
-            const int64_t step = (hi - lo + 31) >> 5;
-            int64_t probe = lo + (lane + 1) * step - 1;
-            if (probe > hi - 1) probe = hi - 1;
-            const unsigned m = __ballot_sync(FULL, a.prefix[probe] > (u128)X);
-            const int f = m ? __ffs(m) - 1 : 31;
-            const int64_t nlo = lo + f * step;
-            const int64_t nhi = min(hi, lo + (f + 1) * step);
-            lo = nlo;
-            hi = nhi;
-        }
-        const int64_t cand = lo + lane;
-        const unsigned mv = __ballot_sync(FULL, cand < hi && a.prefix[cand] > (u128)X);
-        if (!mv) { bad = true; continue; }
-        const uint32_t v = (uint32_t)(lo + __ffs(mv) - 1);
-        const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
-        // ---- entry of v's level-h row, in (shape id, colour mask) order
-        const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
-        V bfr;
-        const int found = (int)warp_first_exceeding<4, V>(a.Wc[h], rem, [&](int64_t e) -> V {
-            const int sh = (int)e / a.Bc[h];
-            const bool ok = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
-            return ok ? (V)vrow[e] : (V)0;
-        }, bfr);
-        if (found < 0) { bad = true; continue; }
-        const int cv0 = a.colors[v];
-        const int s0 = found / a.Bc[h];
-        const unsigned C0 = (1u << cv0) | insert_colour_gap(sm.unrank[h - 1][found % a.Bc[h]], cv0);
-        // ---- descent over the decomposition, pre-order; each stack entry
-        // carries its node's colour
-        int stg[MAXK], stc[MAXK], sp = 0, nn = 0;
-        unsigned stC[MAXK];
-        uint32_t stx[MAXK], nodes[MAXK];
-        stg[0] = a.first[h] + s0; stC[0] = C0; stx[0] = v; stc[0] = cv0; sp = 1;
-        uint32_t step = 0;
-        while (sp > 0) {
-            --sp;
-            const int g = stg[sp];
-            const unsigned C = stC[sp];
-            const uint32_t x = stx[sp];
-            const int cx = stc[sp];
-            if (a.sz[g] == 1) {
-                if (nn >= MAXK) { bad = true; break; }
-                nodes[nn++] = x;
-                continue;
+        bool ok = sid < a.count;
+        // ---- root: X = uniform(R); v = first node with prefix[v] > X, found
+        // by binary search inside the bucket of X
+        V X = 0;
+        uint32_t v = 0;
+        if (ok && !draw_below(a.seed, index, 0, (V)a.R, X)) { ok = false; bad = true; }
+        if (ok) {
+            const uint64_t bk = (uint64_t)(X / (V)a.D);
+            int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
             }
-            ++step;
-            const int ga = a.lft[g], gb = a.rgt[g];
-            const int hb = a.sz[gb];
-            const int64_t e0 = a.row_ptr[x], e1 = a.row_ptr[x + 1];
-            const int chunk0 = a.node_chunk0[x];
-            const V W = (V)a.beta[g] * count_at<CT, V>(a, sm, g, C, x, cx);
-            V Y;
-            if (!draw_below(a.seed, index, step, W, Y)) { bad = true; break; }
-            const unsigned rest = C & ~(1u << cx);
-            const int nr = __popc(rest);
-            int nsub = 1;
-            for (int i = 1; i <= hb; ++i) nsub = nsub * (nr - hb + i) / i;
-            // block of C'' (ascending mask): weights c(T'_{C \ C''}, x) S(T'', C'', x)
-            const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
-            const int sbase = a.loc[gb] * a.Bs[hb];
-            V before;
-            const int blk = (int)warp_first_exceeding<2, V>(nsub, Y, [&](int64_t i) -> V {
-                const unsigned c2 = deposit(sm.unrank[hb][i], rest);
-                return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) * (V)srow[sbase + sm.crank[drop_colour(c2, cx)]];
-            }, before);
-            if (blk < 0) { bad = true; break; }
-            const unsigned C2 = deposit(sm.unrank[hb][blk], rest);
-            const unsigned C1 = C & ~C2;
-            const V x1 = count_at<CT, V>(a, sm, ga, C1, x, cx);
-            const V Yp = Y - before;
-            const CT q = (CT)quotient(Yp, x1);  // q < S(T'', C'', x), which fits the count type
-            // neighbour: first u (ascending) whose running sum of c(T''_{C''}, u)
-            // exceeds q; at a hub, first its 256-neighbour chunk from the
-            // chunk partial sums, then inside that chunk
+            v = (uint32_t)lo;
+            if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
+        }
+        // ---- entry of v's level-h row, in (shape id, colour mask) order
+        int s0 = 0, cv0 = 0;
+        unsigned C0 = 0;
+        if (ok) {
+            const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
+            const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
+            const int Bc = a.Bc[h];
+            V bf;
+            const int found = lane_first_exceeding<V>(a.Wc[h], rem, [&](int e) -> V {
+                const int sh = e / Bc;
+                const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
+                return al ? (V)vrow[e] : (V)0;
+            }, bf);
+            if (found < 0) { ok = false; bad = true; }
+            else {
+                cv0 = a.colors[v];
+                s0 = found / Bc;
+                C0 = (1u << cv0) | insert_colour_gap(sm.unrank[h - 1][found % Bc], cv0);
+            }
+        }
+        // ---- descent: decomposition nodes in pre-order (T' before T'')
+        int stg[MAXK], stc[MAXK], sp = 0, nn = 0, ne = 0;
+        unsigned stC[MAXK];
+        uint32_t stx[MAXK], nodes[MAXK], ea[MAXK], eb[MAXK];
+        if (ok) { stg[0] = a.first[h] + s0; stC[0] = C0; stx[0] = v; stc[0] = cv0; sp = 1; }
+        for (uint32_t step = 1; step < (uint32_t)h; ++step) {
+            int g = 0, cx = 0;
+            unsigned C = 0;
+            uint32_t x = 0;
+            if (ok) {  // leaves on top of the stack are sample nodes
+                for (;;) {
+                    if (sp <= 0 || nn >= MAXK) { ok = false; bad = true; break; }
+                    --sp;
+                    g = stg[sp]; C = stC[sp]; x = stx[sp]; cx = stc[sp];
+                    if (a.sz[g] > 1) break;
+                    nodes[nn++] = x;
+                }
+            }
+            int ga = 0, gb = 0, hb = 1, sbase = 0, sidx = 0, chunk0 = -1;
+            unsigned C1 = 0, C2 = 0;
+            int64_t e0 = 0, e1 = 0, nch = 0;
+            CT q = 0;
+            if (ok) {
+                ga = a.lft[g]; gb = a.rgt[g]; hb = a.sz[gb];
+                e0 = a.row_ptr[x];
+                e1 = a.row_ptr[x + 1];
+                chunk0 = a.node_chunk0[x];
+                const V W = (V)a.beta[g] * count_at<CT, V>(a, sm, g, C, x, cx);
+                V Y = 0;
+                if (!draw_below(a.seed, index, step, W, Y)) { ok = false; bad = true; }
+                if (ok) {
+                    // block of C'' (ascending mask), weights c(T'_{C\C''}, x) S(T'', C'', x)
+                    const unsigned rest = C & ~(1u << cx);
+                    const int nr = __popc(rest);
+                    int nsub = 1;
+                    for (int i = 1; i <= hb; ++i) nsub = nsub * (nr - hb + i) / i;
+                    const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
+                    sbase = a.loc[gb] * a.Bs[hb];
+                    V before;
+                    const int blk = lane_first_exceeding<V>(nsub, Y, [&](int i) -> V {
+                        const unsigned c2 = deposit(sm.unrank[hb][i], rest);
+                        return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) *
+                               (V)srow[sbase + sm.crank[drop_colour(c2, cx)]];
+                    }, before);
+                    if (blk < 0) { ok = false; bad = true; }
+                    else {
+                        C2 = deposit(sm.unrank[hb][blk], rest);
+                        C1 = C & ~C2;
+                        const V x1 = count_at<CT, V>(a, sm, ga, C1, x, cx);
+                        q = (CT)quotient(Y - before, x1);  // < S(T'', C'', x): fits CT
+                        sidx = sbase + sm.crank[drop_colour(C2, cx)];
+                        if (chunk0 >= 0) nch = (e1 - e0 + HUB_CHUNK - 1) / HUB_CHUNK;
+                    }
+                }
+            }
+            // ---- hub: the 64-neighbour chunk holding the answer, from the
+            // chunk partial sums (contiguous per hub and entry)
+            const CT *spp = nullptr;
+            if (ok && chunk0 >= 0) spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
+            int64_t ci = -1;
+            CT bc = 0;
+            const bool coop = ok && chunk0 >= 0 && nch > SEQ_CHUNKS;
+            unsigned need = __ballot_sync(FULL, coop);
+            while (need) {
+                const int L = __ffs(need) - 1;
+                need &= need - 1;
+                const CT *sL = (const CT *)__shfl_sync(FULL, (unsigned long long)spp, L);
+                const int64_t nL = (int64_t)__shfl_sync(FULL, (unsigned long long)nch, L);
+                const CT qL = shfl(q, L);
+                CT bL;
+                const int64_t cL = warp_first_exceeding<4, CT>(nL, qL, [&](int64_t i) -> CT { return sL[i]; }, bL);
+                if (lane == L) { ci = cL; bc = bL; }
+            }
+            if (ok && chunk0 >= 0 && !coop)
+                ci = lane_first_exceeding<CT>((int)nch, q, [&](int i) -> CT { return spp[i]; }, bc);
             int64_t lo_e = e0, hi_e = e1;
             CT qq = q;
-            const int sidx = sbase + sm.crank[drop_colour(C2, cx)];
-            if (chunk0 >= 0) {
-                const int64_t nch = (e1 - e0 + HUB_CHUNK - 1) / HUB_CHUNK;
-                // this hub's partial sums of entry sidx, one per chunk, contiguous
-                const CT *spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
-                CT bc;
-                const int64_t ci = warp_first_exceeding<4, CT>(nch, q, [&](int64_t i) -> CT {
-                    return spp[i];
-                }, bc);
-                if (ci < 0) { bad = true; break; }
-                lo_e = e0 + ci * HUB_CHUNK;
-                hi_e = min(e1, lo_e + HUB_CHUNK);
-                qq = q - bc;
+            if (ok && chunk0 >= 0) {
+                if (ci < 0) { ok = false; bad = true; }
+                else {
+                    lo_e = e0 + ci * HUB_CHUNK;
+                    hi_e = min(e1, lo_e + HUB_CHUNK);
+                    qq = q - bc;
+                }
             }
-            const int lb = a.loc[gb];
-            const CT *chb = (const CT *)a.c[hb];
-            const int bcb = a.Bc[hb], wcb = a.Wc[hb];
-            CT bn;
-            const int64_t sel = warp_first_exceeding<(HUB_CHUNK + 31) / 32, CT>(hi_e - lo_e, qq, [&](int64_t i) -> CT {
-                const int cu = a.ecol[lo_e + i];
-                if (!((C2 >> cu) & 1u)) return (CT)0;
-                if (hb == 1) return (CT)1;
-                const uint32_t u = a.col[lo_e + i];
-                return chb[(int64_t)u * wcb + lb * bcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)]];
-            }, bn);
-            if (sel < 0) { bad = true; break; }
-            const uint32_t u = a.col[lo_e + sel];
-            const int cu = a.ecol[lo_e + sel];
-            if (sp + 2 > MAXK) { bad = true; break; }
-            stg[sp] = gb; stC[sp] = C2; stx[sp] = u; stc[sp] = cu; ++sp;
-            stg[sp] = ga; stC[sp] = C1; stx[sp] = x; stc[sp] = cx; ++sp;
+            // ---- neighbour: first u (ascending) whose running sum of
+            // c(T''_{C''}, u) exceeds qq (at most HUB_CHUNK neighbours)
+            if (ok) {
+                int64_t sel = -1;
+                if (hb == 1) {
+                    // the (qq+1)-th neighbour whose colour is the one colour of C''
+                    const int col2 = __ffs(C2) - 1;
+                    uint64_t rank = (uint64_t)qq;
+                    for (int64_t b = lo_e; b < hi_e && sel < 0; b += 8) {
+                        uint8_t cc[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) cc[i] = b + i < hi_e ? a.ecol[b + i] : (uint8_t)0xff;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (sel < 0 && cc[i] == col2) {
+                                if (rank == 0) sel = b + i;
+                                else --rank;
+                            }
+                    }
+                } else {
+                    const int lb = a.loc[gb];
+                    const CT *chb = (const CT *)a.c[hb];
+                    const int bcb = a.Bc[hb], wcb = a.Wc[hb];
+                    CT bn;
+                    const int r = lane_first_exceeding<CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
+                        const int cu = a.ecol[lo_e + i];
+                        if (!((C2 >> cu) & 1u)) return (CT)0;
+                        const uint32_t u = a.col[lo_e + i];
+                        return chb[(int64_t)u * wcb + lb * bcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)]];
+                    }, bn);
+                    if (r >= 0) sel = lo_e + r;
+                }
+                if (sel < 0 || sp + 2 > MAXK || ne >= MAXK) { ok = false; bad = true; }
+                else {
+                    const uint32_t u = a.col[sel];
+                    const int cu = a.ecol[sel];
+                    ea[ne] = x; eb[ne] = u; ++ne;   // a treelet edge: adjacent for sure
+                    stg[sp] = gb; stC[sp] = C2; stx[sp] = u; stc[sp] = cu; ++sp;
+                    stg[sp] = ga; stC[sp] = C1; stx[sp] = x; stc[sp] = cx; ++sp;
+                }
+            }
         }
-        if (nn != h) { bad = true; continue; }
-        for (int i = 1; i < h; ++i)
-            for (int j = i; j > 0 && nodes[j - 1] > nodes[j]; --j) {
-                const uint32_t tmp = nodes[j]; nodes[j] = nodes[j - 1]; nodes[j - 1] = tmp;
+        if (ok) {  // remaining leaves
+            while (sp > 0 && nn < MAXK) { --sp; nodes[nn++] = stx[sp]; }
+            if (nn != h || sp != 0) { ok = false; bad = true; }
+        }
+        int cls = -1;
+        if (ok) {
+            for (int i = 1; i < h; ++i)
+                for (int j = i; j > 0 && nodes[j - 1] > nodes[j]; --j) {
+                    const uint32_t tmp = nodes[j]; nodes[j] = nodes[j - 1]; nodes[j - 1] = tmp;
+                }
+            // induced subgraph: the treelet's edges are known; the other pairs
+            // are tested against the adjacency lists, four at a time
+            const int P = h * (h - 1) / 2;
+            uint32_t word = 0, known = 0;
+            for (int t = 0; t < ne; ++t) {
+                int i = 0, j = 0;
+                for (int p = 0; p < h; ++p) {
+                    if (nodes[p] == ea[t]) i = p;
+                    if (nodes[p] == eb[t]) j = p;
+                }
+                if (i > j) { const int tmp = i; i = j; j = tmp; }
+                known |= 1u << pair_pos(h, i, j);
             }
-        // ---- classify: lane p tests pair p
-        const int P = h * (h - 1) / 2;
-        bool adj = false;
-        if (lane < P) adj = adjacent(a.row_ptr, a.col, nodes[a.pi[lane]], nodes[a.pj[lane]]);
-        const unsigned bal = __ballot_sync(FULL, adj);
-        const uint32_t word = __brev(bal) >> (32 - P);
-        const int cls = a.lut[word];
-        if (cls == 0xffff) bad = true;
-        if (lane == 0) {
+            word = known;
+            uint32_t qa[4], qb[4];
+            int qp[4], nq = 0;
+            for (int p = 0; p < P; ++p) {
+                const int i = a.pi[p], j = a.pj[p];
+                const int bit = pair_pos(h, i, j);
+                if ((known >> bit) & 1u) continue;
+                qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
+                if (nq == 4 || p == P - 1) {
+                    bool r4[4];
+                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4);
+                    for (int t = 0; t < nq; ++t)
+                        if (r4[t]) word |= 1u << qp[t];
+                    nq = 0;
+                }
+            }
+            if (nq) {
+                bool r4[4];
+                adjacent4(a.row_ptr, a.col, qa, qb, nq, r4);
+                for (int t = 0; t < nq; ++t)
+                    if (r4[t]) word |= 1u << qp[t];
+            }
+            cls = a.lut[word];
+            if (cls == 0xffff) { cls = -1; bad = true; }
             if (a.nodes) for (int i = 0; i < h; ++i) a.nodes[sid * h + i] = nodes[i];
             if (a.roots) a.roots[sid] = v;
             if (a.shapes) a.shapes[sid] = s0;
-            if (a.classes) a.classes[sid] = cls == 0xffff ? -1 : cls;
-            if (a.hist && cls != 0xffff) atomicAdd(&s_hist[cls], 1u);
+            if (a.hist && cls >= 0) atomicAdd(&s_hist[cls], 1u);
         }
+        if (sid < a.count && a.classes) a.classes[sid] = cls;
     }
     if (bad) atomicOr(a.err, SERR_SEARCH);
     if (a.hist) {
@@ -710,7 +856,7 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     int per_sm = 0;
     MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (a.count * 32 + block - 1) / block;
+    int64_t grid = (a.count + block - 1) / block;  // one sample per thread
     const int64_t cap = (int64_t)sm_count() * per_sm;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
