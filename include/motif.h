@@ -190,7 +190,9 @@ mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *param
  *    allocation); make that first call before any stream capture.
  *  - The graphlet catalogue of size h must already exist on the device
  *    (mc_sigma(h), mc_num_classes(h) with mc_sigma, or mc_estimate_counts
- *    create it); otherwise MC_E_INVALID, since creating it allocates.
+ *    create it); otherwise MC_E_INVALID, since creating it allocates.  For
+ *    h < k the same holds for the level's root index (mc_total(t, h, -1, ...)
+ *    or any sampling at that h creates it).
  *  - All calls share the one scratch array, cleared at the start of each
  *    call: calls whose work overlaps on the GPU (other streams, other host
  *    threads) race and must be serialised by the caller.

@@ -185,7 +185,7 @@ class Graph:
         lib = load()
         torch = _torch()
         on_dev = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
-        if not on_dev:
+        if not hasattr(row_ptr, "data_ptr"):  # numpy input; torch CPU tensors (e.g. pinned) pass as is
             row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
             col = np.ascontiguousarray(col, dtype=np.uint32)
         n = int(row_ptr.shape[0]) - 1

@@ -28,23 +28,19 @@ __global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict_
                                                       const uint8_t *__restrict__ colors, int64_t n,
                                                       int k, CT *__restrict__ S1)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        const int cv = colors[v];
+    // one thread per node of degree <= HUB_CHUNK (hubs: their chunk counts
+    // are summed by hub_reduce); per-colour counts packed one byte each
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-        uint32_t cnt = 0;  // lane a (< k-1) counts relative colour a
-        for (int64_t b = e0; b < e1; b += 32) {
-            const int64_t e = b + lane;
-            const int cu = e < e1 ? (int)ecol[e] : -1;
-            for (int a = 0; a < k - 1; ++a) {
-                const int abs_a = a < cv ? a : a + 1;
-                const unsigned m = __ballot_sync(0xffffffffu, cu == abs_a);
-                if (lane == a) cnt += __popc(m);
-            }
+        if (e1 - e0 > HUB_CHUNK) continue;
+        uint64_t acc = 0;
+        for (int64_t e = e0; e < e1; ++e) acc += 1ull << (8 * ecol[e]);
+        const int cv = colors[v];
+        for (int a = 0; a < k - 1; ++a) {
+            const int abs_a = a < cv ? a : a + 1;
+            S1[v * (k - 1) + a] = (CT)((acc >> (8 * abs_a)) & 0xffu);
         }
-        if (lane < k - 1) S1[v * (k - 1) + lane] = (CT)cnt;
     }
 }
 
@@ -552,11 +548,15 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
     const int64_t n = g->n;
     if (n == 0) return;
     // level 1 neighbour sums
-    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, t->ecol, t->colors, n, k, (CT *)t->S[1]));
+    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n, 256), 256, 0, s>>>(g->row_ptr, t->ecol, t->colors, n, k, (CT *)t->S[1]));
     if (g->n_chunks && k >= 2)
         MC_LAUNCH("chunk_h1", s, chunk1_kernel<CT><<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
                                      t->ecol, t->colors, g->chunk_node, g->chunk_e0, g->chunk_e1, g->node_chunk0,
                                      g->row_ptr, g->n_chunks, k, (CT *)t->Sp[1]));
+    if (g->n_hubs)
+        MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[1], 256), 256, 0, s>>>(
+                                       (const CT *)t->Sp[1], (CT *)t->S[1], g->hub_node, g->hub_chunk0, g->n_hubs,
+                                       G.Ws[1], err));
 
     MergeArgs ma{};
     for (int h = 1; h <= k; ++h) {
@@ -670,25 +670,25 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         for (int h = 2; h <= k; ++h) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
         for (int h = 1; h <= k - 1; ++h) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
         for (int h = 1; h <= k - 1; ++h) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
-        for (int h = 2; h <= k; ++h) t->prefix[h] = t->arena.get<u128>((size_t)n);
+
         if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
         else build_levels<u128>(t, err, scratch, s);
         // node prefixes of the level totals, for the root draw
+        // root index of the top level (the level sampled by default); the
+        // other levels get theirs on first use
         t->nbucket = bucket_count(n);
-        u128 *dD = scratch.get<u128>(MAXK + 1);
-        for (int h = 2; h <= k; ++h) {
-            launch_row_totals(t, h, ~0ull, ~0ull, t->prefix[h], err, s);
-            inclusive_scan_u128(t->prefix[h], n, err, scratch, s);
-            t->bucket[h] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
-            build_buckets(t->prefix[h], n, t->nbucket, dD + h, t->bucket[h], s);
-        }
+        u128 *dD = scratch.get<u128>(1);
+        t->prefix[k] = t->arena.get<u128>((size_t)n);
+        t->bucket[k] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
+        launch_row_totals(t, k, ~0ull, ~0ull, t->prefix[k], err, s);
+        inclusive_scan_u128(t->prefix[k], n, err, scratch, s);
+        build_buckets(t->prefix[k], n, t->nbucket, dD, t->bucket[k], s);
         int herr = 0;
         MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        for (int h = 2; h <= k; ++h)
-            if (n) {
-                MC_CUDA(cudaMemcpyAsync(&t->R[h], t->prefix[h] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
-                MC_CUDA(cudaMemcpyAsync(&t->bucketD[h], dD + h, sizeof(u128), cudaMemcpyDeviceToHost, s));
-            }
+        if (n) {
+            MC_CUDA(cudaMemcpyAsync(&t->R[k], t->prefix[k] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(&t->bucketD[k], dD, sizeof(u128), cudaMemcpyDeviceToHost, s));
+        }
         MC_CUDA(cudaStreamSynchronize(s));
         if (herr & ERR_COLOUR) throw Error(MC_E_INVALID, "a colour is >= k");
         if (herr & ERR_OVERFLOW)
@@ -698,6 +698,38 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
     if (st != MC_OK) { delete t; return st; }
     *out = t;
     return MC_OK;
+}
+
+void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
+{
+    mc_tables *t = const_cast<mc_tables *>(tc);
+    std::lock_guard<std::mutex> lock(t->idx_mu);
+    if (t->prefix[h] || h < 2) return;
+    const int64_t n = t->g->n;
+    Arena scratch;
+    scratch.alloc = t->arena.alloc;
+    scratch.stream = s;
+    int *err = scratch.get<int>(1);
+    u128 *dD = scratch.get<u128>(1);
+    MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    u128 *p = t->arena.get<u128>((size_t)n);
+    uint32_t *bk = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
+    launch_row_totals(t, h, ~0ull, ~0ull, p, err, s);
+    inclusive_scan_u128(p, n, err, scratch, s);
+    build_buckets(p, n, t->nbucket, dD, bk, s);
+    u128 R = 0, D = 1;
+    int herr = 0;
+    if (n) {
+        MC_CUDA(cudaMemcpyAsync(&R, p + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(&D, dD, sizeof(u128), cudaMemcpyDeviceToHost, s));
+    }
+    MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error(MC_E_OVERFLOW, "a level total does not fit in 128 bits");
+    t->R[h] = R;
+    t->bucketD[h] = D;
+    t->bucket[h] = bk;
+    t->prefix[h] = p;  // published last
 }
 
 extern "C" void mc_free_tables(mc_tables *t) { delete t; }
@@ -715,6 +747,7 @@ extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape,
             R = (u128)t->g->n;
             if (unrooted_shape > 0) R = 0;
         } else if (unrooted_shape < 0) {
+            ensure_level_index(t, h, (cudaStream_t)stream);
             R = t->R[h];
         } else if (t->g->n > 0) {
             cudaStream_t s = (cudaStream_t)stream;

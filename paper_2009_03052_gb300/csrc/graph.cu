@@ -9,6 +9,8 @@
 
 namespace mc {
 
+void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s);
+
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
@@ -69,6 +71,57 @@ __global__ void validate_edges(const int64_t *row_ptr, const uint32_t *col, int6
         }
         if (lo >= row_ptr[w + 1] || col[lo] != (uint32_t)u) atomicOr(flags, 8);
     }
+}
+
+__global__ void validate_offsets(const int64_t *row_ptr, int64_t n, int64_t nnz, int *flags)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (v == 0 && row_ptr[0] != 0) atomicOr(flags, 16);
+        if (v == n && row_ptr[n] != nnz) atomicOr(flags, 16);
+        if (v < n && row_ptr[v] > row_ptr[v + 1]) atomicOr(flags, 16);
+    }
+}
+
+// per node: number of hub chunks (0 unless degree > HUB_CHUNK) and whether
+// it is a hub; the largest degree
+__global__ void degree_stats(const int64_t *row_ptr, int64_t n, u128 *nch, u128 *nhub, unsigned long long *maxdeg)
+{
+    unsigned long long md = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        nch[v] = d > HUB_CHUNK ? (u128)((d + HUB_CHUNK - 1) / HUB_CHUNK) : (u128)0;
+        nhub[v] = d > HUB_CHUNK ? 1 : 0;
+        if ((unsigned long long)d > md) md = (unsigned long long)d;
+    }
+    atomicMax(maxdeg, md);
+}
+
+// from the inclusive prefixes of chunk and hub counts: every hub writes its
+// chunks (node, first edge, end edge), its entry in the hub list and its
+// first chunk
+__global__ void hub_chunks(const int64_t *row_ptr, int64_t n, const u128 *nch, const u128 *nhub,
+                           uint32_t *chunk_node, int64_t *chunk_e0, int64_t *chunk_e1, uint32_t *hub_node,
+                           int64_t *hub_chunk0, int32_t *node_chunk0, int64_t n_hubs, int64_t n_chunks)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c1 = (int64_t)nch[v], c0 = v ? (int64_t)nch[v - 1] : 0;
+        if (c1 == c0) { node_chunk0[v] = -1; continue; }
+        const int64_t hid = (int64_t)nhub[v] - 1;
+        hub_node[hid] = (uint32_t)v;
+        hub_chunk0[hid] = c0;
+        if (hid == n_hubs - 1) hub_chunk0[n_hubs] = n_chunks;
+        node_chunk0[v] = (int32_t)c0;
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        for (int64_t c = c0; c < c1; ++c) {
+            chunk_node[c] = (uint32_t)v;
+            chunk_e0[c] = e0 + (c - c0) * HUB_CHUNK;
+            chunk_e1[c] = min(e1, e0 + (c - c0 + 1) * HUB_CHUNK);
+        }
+    }
+    if (n_hubs == 0 && blockIdx.x == 0 && threadIdx.x == 0) hub_chunk0[0] = 0;
 }
 
 // Colouring: c_v = floor(k * x0 / 2^32), x0 the first Philox4x32-10 word at
@@ -254,68 +307,75 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
         g->n = n;
         g->nnz = nnz;
         const bool on_dev = flags & MC_GRAPH_DEVICE_PTRS;
+        const bool trusted = flags & MC_GRAPH_TRUSTED;
         const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        Arena scratch;
+        scratch.alloc = g->arena.alloc;
+        scratch.stream = s;
+        int64_t *dstat = scratch.get<int64_t>(4);  // flags, max degree, #chunks, #hubs
+        MC_CUDA(cudaMemsetAsync(dstat, 0, 4 * sizeof(int64_t), s));
         g->row_ptr = g->arena.get<int64_t>((size_t)n + 1);
         g->col = g->arena.get<uint32_t>((size_t)(nnz > 0 ? nnz : 1));
         MC_CUDA(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, s));
         if (nnz) MC_CUDA(cudaMemcpyAsync(g->col, col, sizeof(uint32_t) * nnz, kind, s));
-        // host copy of the offsets, for degree statistics and hub chunks
-        std::vector<int64_t> rp((size_t)n + 1);
-        MC_CUDA(cudaMemcpyAsync(rp.data(), g->row_ptr, sizeof(int64_t) * (n + 1),
-                                cudaMemcpyDeviceToHost, s));
-        MC_CUDA(cudaStreamSynchronize(s));
-        MC_REQUIRE(rp[0] == 0 && rp[n] == nnz, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
-        // offsets are checked here, before any kernel indexes with them
-        for (int64_t v = 0; v < n; ++v)
-            MC_REQUIRE(rp[v] <= rp[v + 1], "row_ptr must be non-decreasing");
-        if (!(flags & MC_GRAPH_TRUSTED) && n > 0) {
-            int *dflags = g->arena.get<int>(1);
-            MC_CUDA(cudaMemsetAsync(dflags, 0, sizeof(int), s));
-            if (nnz)
-                MC_LAUNCH("validate_edges", s,
-                          validate_edges<<<grid_for(nnz, 256), 256, 0, s>>>(g->row_ptr, g->col, n, nnz, dflags));
-            int hf = 0;
-            MC_CUDA(cudaMemcpyAsync(&hf, dflags, sizeof(int), cudaMemcpyDeviceToHost, s));
-            MC_CUDA(cudaStreamSynchronize(s));
-            MC_REQUIRE(hf == 0, "graph is not a canonical symmetric CSR (flags " + std::to_string(hf) +
-                                    ": 1 range, 2 loop, 4 order/duplicate, 8 asymmetric)");
-        }
-        // degree statistics and hub chunks
-        std::vector<uint32_t> cn, hn;
-        std::vector<int64_t> c0, c1, h0;
-        for (int64_t v = 0; v < n; ++v) {
-            const int64_t d = rp[v + 1] - rp[v];
-            g->max_degree = std::max(g->max_degree, d);
-            if (d > HUB_CHUNK) {
-                hn.push_back((uint32_t)v);
-                h0.push_back((int64_t)cn.size());
-                for (int64_t e = rp[v]; e < rp[v + 1]; e += HUB_CHUNK) {
-                    cn.push_back((uint32_t)v);
-                    c0.push_back(e);
-                    c1.push_back(std::min(e + HUB_CHUNK, rp[v + 1]));
-                }
+        // the offsets are checked before any kernel indexes with them: on the
+        // host for host input, by a kernel (and a read-back) for device input
+        if (!trusted) {
+            if (!on_dev) {
+                MC_REQUIRE(row_ptr[0] == 0 && row_ptr[n] == nnz, "row_ptr[0] must be 0 and row_ptr[n] must be nnz");
+                for (int64_t v = 0; v < n; ++v)
+                    MC_REQUIRE(row_ptr[v] <= row_ptr[v + 1], "row_ptr must be non-decreasing");
+            } else {
+                MC_LAUNCH("validate_offsets", s, validate_offsets<<<grid_for(n + 1, 256), 256, 0, s>>>(
+                                                     g->row_ptr, n, nnz, (int *)dstat));
+                int hf = 0;
+                MC_CUDA(cudaMemcpyAsync(&hf, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaStreamSynchronize(s));
+                MC_REQUIRE(hf == 0, "row_ptr must start at 0, end at nnz and be non-decreasing");
             }
+            if (n > 0 && nnz)
+                MC_LAUNCH("validate_edges", s, validate_edges<<<grid_for(nnz, 256), 256, 0, s>>>(
+                                                   g->row_ptr, g->col, n, nnz, (int *)dstat));
         }
-        h0.push_back((int64_t)cn.size());
-        MC_REQUIRE(cn.size() < (size_t)0x7fffffff, "too many hub chunks");
-        std::vector<int32_t> nc0((size_t)n, -1);
-        for (size_t i = 0; i < hn.size(); ++i) nc0[hn[i]] = (int32_t)h0[i];
+        // hub chunks, built on the device: chunk counts per node, their
+        // prefix, then one thread per hub writes its chunks
+        u128 *nch = scratch.get<u128>((size_t)(n > 0 ? n : 1));
+        u128 *nhub = scratch.get<u128>((size_t)(n > 0 ? n : 1));
+        int *serr = scratch.get<int>(1);
+        MC_CUDA(cudaMemsetAsync(serr, 0, sizeof(int), s));
+        if (n > 0) {
+            MC_LAUNCH("degree_stats", s, degree_stats<<<grid_for(n, 256), 256, 0, s>>>(
+                                             g->row_ptr, n, nch, nhub, (unsigned long long *)(dstat + 1)));
+            inclusive_scan_u128(nch, n, serr, scratch, s);
+            inclusive_scan_u128(nhub, n, serr, scratch, s);
+        }
+        int64_t hst[4] = {0, 0, 0, 0};
+        MC_CUDA(cudaMemcpyAsync(hst, dstat, sizeof(hst), cudaMemcpyDeviceToHost, s));
+        u128 tails[2] = {0, 0};
+        if (n > 0) {
+            MC_CUDA(cudaMemcpyAsync(&tails[0], nch + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(&tails[1], nhub + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        }
+        MC_CUDA(cudaStreamSynchronize(s));
+        MC_REQUIRE(((int *)hst)[0] == 0, "graph is not a canonical symmetric CSR (flags " +
+                                             std::to_string(((int *)hst)[0]) +
+                                             ": 1 range, 2 loop, 4 order/duplicate, 8 asymmetric)");
+        g->max_degree = hst[1];
+        g->n_chunks = (int64_t)tails[0];
+        g->n_hubs = (int64_t)tails[1];
+        MC_REQUIRE(g->n_chunks < (int64_t)0x7fffffff, "too many hub chunks");
+        g->chunk_node = g->arena.get<uint32_t>((size_t)g->n_chunks);
+        g->chunk_e0 = g->arena.get<int64_t>((size_t)g->n_chunks);
+        g->chunk_e1 = g->arena.get<int64_t>((size_t)g->n_chunks);
+        g->hub_node = g->arena.get<uint32_t>((size_t)g->n_hubs);
+        g->hub_chunk0 = g->arena.get<int64_t>((size_t)g->n_hubs + 1);
         g->node_chunk0 = g->arena.get<int32_t>((size_t)n);
-        if (n) MC_CUDA(cudaMemcpyAsync(g->node_chunk0, nc0.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
-        g->n_hubs = (int64_t)hn.size();
-        g->n_chunks = (int64_t)cn.size();
-        g->chunk_node = g->arena.get<uint32_t>(cn.size());
-        g->chunk_e0 = g->arena.get<int64_t>(c0.size());
-        g->chunk_e1 = g->arena.get<int64_t>(c1.size());
-        g->hub_node = g->arena.get<uint32_t>(hn.size());
-        g->hub_chunk0 = g->arena.get<int64_t>(h0.size());
-        if (!cn.empty()) {
-            MC_CUDA(cudaMemcpyAsync(g->chunk_node, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
-            MC_CUDA(cudaMemcpyAsync(g->chunk_e0, c0.data(), c0.size() * 8, cudaMemcpyHostToDevice, s));
-            MC_CUDA(cudaMemcpyAsync(g->chunk_e1, c1.data(), c1.size() * 8, cudaMemcpyHostToDevice, s));
-            MC_CUDA(cudaMemcpyAsync(g->hub_node, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice, s));
-        }
-        MC_CUDA(cudaMemcpyAsync(g->hub_chunk0, h0.data(), h0.size() * 8, cudaMemcpyHostToDevice, s));
+        if (n > 0)
+            MC_LAUNCH("hub_chunks", s, hub_chunks<<<grid_for(n, 256), 256, 0, s>>>(
+                                           g->row_ptr, n, nch, nhub, g->chunk_node, g->chunk_e0, g->chunk_e1,
+                                           g->hub_node, g->hub_chunk0, g->node_chunk0, g->n_hubs, g->n_chunks));
+        else
+            MC_CUDA(cudaMemsetAsync(g->hub_chunk0, 0, sizeof(int64_t), s));
         MC_CUDA(cudaStreamSynchronize(s));
     });
     if (st != MC_OK) { delete g; return st; }

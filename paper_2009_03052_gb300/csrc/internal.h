@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -102,6 +103,10 @@ void prof_end(ProfSpan &span, cudaStream_t s);
             throw ::mc::Error(MC_E_CUDA, std::string(name) + ": " + cudaGetErrorString(le_)); \
     } while (0)
 
+// Make sure level h's root index (node prefix of the level totals, R and
+// the root-search buckets) exists; builds and publishes it on first use.
+void ensure_level_index(const mc_tables *t, int h, cudaStream_t s);
+
 // Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
 // partial sums are added afterwards.
@@ -109,6 +114,7 @@ constexpr int HUB_CHUNK = 64;
 
 }  // namespace mc
 
+struct mc_tables;
 struct mc_graph {
     int64_t n = 0, nnz = 0, max_degree = 0;
     int64_t *row_ptr = nullptr;  // device int64[n+1]
@@ -134,6 +140,9 @@ struct mc_tables {
     void *Sp[mc::MAXK + 1] = {nullptr};        // level h <= k-1: hub chunk partial sums, n_chunks x Ws[h]
     mc::u128 *prefix[mc::MAXK + 1] = {nullptr};  // inclusive node prefix of level totals
     mc::u128 R[mc::MAXK + 1] = {0};            // rooted totals
+    // root index of a level (node prefix, R, buckets): level k at build,
+    // other levels on first use (guarded by idx_mu)
+    std::mutex idx_mu;
     uint32_t *bucket[mc::MAXK + 1] = {nullptr}; // root-search buckets over [0, R) (see sample.cu)
     mc::u128 bucketD[mc::MAXK + 1] = {0};
     int64_t nbucket = 0;

@@ -495,10 +495,10 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 // lane's search after another.  CT: the tables' count type; V: the type of
 // the descent's weights, draws and running sums (64 bits when every level
 // total leaves room for beta, else 128 bits).
-constexpr int SEQ_CHUNKS = 16;
+constexpr int SEQ_CHUNKS = 64;
 
 template <typename CT, typename V>
-__global__ void __launch_bounds__(256) sample_kernel(const __grid_constant__ SampleArgs a)
+__global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ SampleArgs a)
 {
     extern __shared__ unsigned int s_hist[];
     __shared__ SampleSmem sm;
@@ -818,6 +818,7 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
         }
     RootIndex ri;
     if (unrooted < 0) {
+        ensure_level_index(t, h, s);
         ri.prefix = t->prefix[h];
         ri.R = t->R[h];
         ri.bucket = t->bucket[h];
@@ -1211,6 +1212,9 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         if (ncls > NOALLOC_MAX_CLASSES)
             throw Error(MC_E_UNSUPPORTED, "more graphlet classes than the static scratch holds (" +
                                               std::to_string(NOALLOC_MAX_CLASSES) + ")");
+        if (!t->prefix[h])
+            throw Error(MC_E_INVALID, "the root index of this level does not exist yet (creating it allocates); "
+                                      "call mc_total(h) first");
         if (t->R[h] == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
         cudaStream_t s = (cudaStream_t)stream;
         NoAllocScratch *scr = noalloc_scratch();
