@@ -22,63 +22,6 @@ enum : int { ERR_OVERFLOW = 1, ERR_INEXACT = 2, ERR_COLOUR = 4, ERR_SEARCH = 8 }
 // level 1: S_1(v)[{a}] = number of neighbours of colour a != c_v
 // (c(single node, {c_u}, u) = 1).  One warp per node; one ballot per colour.
 // ---------------------------------------------------------------------------
-template <typename CT>
-__global__ void __launch_bounds__(256) gather1_kernel(const int64_t *__restrict__ row_ptr,
-                                                      const uint8_t *__restrict__ ecol,
-                                                      const uint8_t *__restrict__ colors, int64_t n,
-                                                      int k, CT *__restrict__ S1)
-{
-    // one thread per node of degree <= HUB_CHUNK (hubs: their chunk counts
-    // are summed by hub_reduce); per-colour counts packed one byte each
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
-        if (e1 - e0 > HUB_CHUNK) continue;
-        uint64_t acc = 0;
-        for (int64_t e = e0; e < e1; ++e) acc += 1ull << (8 * ecol[e]);
-        const int cv = colors[v];
-        for (int a = 0; a < k - 1; ++a) {
-            const int abs_a = a < cv ? a : a + 1;
-            S1[v * (k - 1) + a] = (CT)((acc >> (8 * abs_a)) & 0xffu);
-        }
-    }
-}
-
-// Level-1 partial sums of each hub chunk (colour counts of its neighbours),
-// kept with the tables for the sampler's chunk skipping.
-template <typename CT>
-__global__ void __launch_bounds__(256) chunk1_kernel(const uint8_t *__restrict__ ecol,
-                                                     const uint8_t *__restrict__ colors,
-                                                     const uint32_t *__restrict__ chunk_node,
-                                                     const int64_t *__restrict__ chunk_e0,
-                                                     const int64_t *__restrict__ chunk_e1,
-                                                     const int32_t *__restrict__ node_chunk0,
-                                                     const int64_t *__restrict__ row_ptr, int64_t n_chunks,
-                                                     int k, CT *__restrict__ Sp1)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = warp; c < n_chunks; c += nwarps) {
-        const uint32_t v = chunk_node[c];
-        const int cv = colors[v];
-        const int64_t e0 = chunk_e0[c], e1 = chunk_e1[c];
-        const int64_t c0 = node_chunk0[v];
-        const int64_t nch = (row_ptr[v + 1] - row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
-        uint32_t cnt = 0;
-        for (int64_t b = e0; b < e1; b += 32) {
-            const int64_t e = b + lane;
-            const int cu = e < e1 ? (int)ecol[e] : -1;
-            for (int a = 0; a < k - 1; ++a) {
-                const int abs_a = a < cv ? a : a + 1;
-                const unsigned m = __ballot_sync(0xffffffffu, cu == abs_a);
-                if (lane == a) cnt += __popc(m);
-            }
-        }
-        if (lane < k - 1) Sp1[c0 * (k - 1) + lane * nch + (c - c0)] = (CT)cnt;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // level h >= 2 neighbour sums.  One warp per task; a task is a node (all its
 // neighbours) or a chunk of HUB_CHUNK neighbours of a hub, whose partial row
@@ -402,6 +345,170 @@ __global__ void edge_colours_kernel(const uint32_t *__restrict__ col, const uint
         ecol[e] = colors[col[e]];
 }
 
+// Colour blocks: every node's neighbour list stably partitioned by the
+// neighbours' colours (scol), with the block starts (coff, k+1 per node).
+// Nodes of degree <= HUB_CHUNK: one thread each, per-colour counts and
+// cursors packed one byte per colour.
+// The per-colour counts are also the level-1 neighbour sums S_1(v)[{a}]
+// (c of a single node is 1 at its own colour), written here too.
+template <typename CT>
+__global__ void colour_blocks_kernel(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                                     const uint8_t *__restrict__ ecol, const uint8_t *__restrict__ colors,
+                                     int64_t n, int k, uint32_t *__restrict__ scol, int32_t *__restrict__ coff,
+                                     CT *__restrict__ S1)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
+        if (e1 - e0 > HUB_CHUNK) continue;
+        uint64_t cnt = 0;
+        for (int64_t e = e0; e < e1; ++e) cnt += 1ull << (8 * ecol[e]);
+        uint64_t cur = 0;  // exclusive prefix of the counts, one byte per colour
+        uint32_t run = 0;
+        for (int a = 0; a < k; ++a) {
+            coff[v * (k + 1) + a] = (int32_t)run;
+            cur |= (uint64_t)run << (8 * a);
+            run += (uint32_t)((cnt >> (8 * a)) & 0xffu);
+        }
+        coff[v * (k + 1) + k] = (int32_t)run;
+        const int cv = colors[v];
+        for (int a = 0; a < k - 1; ++a) {
+            const int abs_a = a < cv ? a : a + 1;
+            S1[v * (k - 1) + a] = (CT)((cnt >> (8 * abs_a)) & 0xffu);
+        }
+        for (int64_t e = e0; e < e1; ++e) {
+            const int c = ecol[e];
+            const uint32_t pos = (uint32_t)((cur >> (8 * c)) & 0xffu);
+            cur += 1ull << (8 * c);
+            scol[e0 + pos] = col[e];
+        }
+    }
+}
+
+// The same for hubs, one warp per hub: per-colour ballots give each edge's
+// rank among the earlier edges of its colour.
+// Hubs: the same, spread over their 64-neighbour chunks so no warp walks a
+// whole hub.  (1) per chunk, per-colour counts; (2) per hub, the exclusive
+// prefix of those counts over its chunks (each chunk's start inside every
+// colour block), the block starts and S_1; (3) per chunk, the scatter.
+static_assert(HUB_CHUNK <= 64, "hub chunk kernels read two 32-edge rounds per chunk");
+
+__global__ void hub_chunk_counts_kernel(const uint8_t *__restrict__ ecol, const int64_t *__restrict__ chunk_e0,
+                                        const int64_t *__restrict__ chunk_e1, int64_t n_chunks, int k,
+                                        uint32_t *__restrict__ ccnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < n_chunks; c += nwarps) {
+        const int64_t e0 = chunk_e0[c], e1 = chunk_e1[c];
+        const int c0 = e0 + lane < e1 ? (int)ecol[e0 + lane] : -1;
+        const int c1 = e0 + 32 + lane < e1 ? (int)ecol[e0 + 32 + lane] : -1;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int a = 0; a < MAXK; ++a)
+            if (a < k) {
+                const uint32_t x = __popc(__ballot_sync(0xffffffffu, c0 == a)) +
+                                   __popc(__ballot_sync(0xffffffffu, c1 == a));
+                if (lane == a) mine = x;
+            }
+        if (lane < k) ccnt[c * k + lane] = mine;
+    }
+}
+
+template <typename CT>
+__global__ void hub_chunk_prefix_kernel(const uint8_t *__restrict__ colors, const uint32_t *__restrict__ hub_node,
+                                        const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int k,
+                                        uint32_t *__restrict__ ccnt, int32_t *__restrict__ coff,
+                                        CT *__restrict__ S1)
+{
+    // one warp per hub: lanes take 32 chunks at a time; a warp scan per
+    // colour turns the counts, in place, into each chunk's start inside that
+    // colour's block
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t hb = warp; hb < n_hubs; hb += nwarps) {
+        const int64_t v = hub_node[hb];
+        const int64_t c0 = hub_chunk0[hb], c1 = hub_chunk0[hb + 1];
+        uint32_t tot[MAXK];
+#pragma unroll
+        for (int a = 0; a < MAXK; ++a) tot[a] = 0;
+        for (int64_t b = c0; b < c1; b += 32) {
+            const int64_t c = b + lane;
+#pragma unroll
+            for (int a = 0; a < MAXK; ++a)
+                if (a < k) {
+                    const uint32_t x = c < c1 ? ccnt[c * k + a] : 0u;
+                    uint32_t inc = x;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (lane >= d) inc += y;
+                    }
+                    if (c < c1) ccnt[c * k + a] = tot[a] + inc - x;
+                    tot[a] += __shfl_sync(0xffffffffu, inc, 31);
+                }
+        }
+        if (lane == 0) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int a = 0; a < MAXK; ++a)
+                if (a < k) {
+                    coff[v * (k + 1) + a] = (int32_t)run;
+                    run += tot[a];
+                }
+            coff[v * (k + 1) + k] = (int32_t)run;
+            const int cv = colors[v];
+#pragma unroll
+            for (int a = 0; a < MAXK - 1; ++a)
+                if (a < k - 1) S1[v * (k - 1) + a] = (CT)tot[a < cv ? a : a + 1];
+        }
+    }
+}
+
+__global__ void hub_chunk_scatter_kernel(const uint32_t *__restrict__ col, const uint8_t *__restrict__ ecol,
+                                         const int64_t *__restrict__ row_ptr,
+                                         const uint32_t *__restrict__ chunk_node,
+                                         const int64_t *__restrict__ chunk_e0, const int64_t *__restrict__ chunk_e1,
+                                         int64_t n_chunks, int k, const uint32_t *__restrict__ cstart,
+                                         const int32_t *__restrict__ coff, uint32_t *__restrict__ scol)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < n_chunks; c += nwarps) {
+        const int64_t v = chunk_node[c];
+        const int64_t base = row_ptr[v];
+        const int64_t e0 = chunk_e0[c], e1 = chunk_e1[c];
+        int cc[2];
+        uint32_t uu[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int64_t e = e0 + 32 * r + lane;
+            cc[r] = e < e1 ? (int)ecol[e] : -1;
+            uu[r] = e < e1 ? col[e] : 0u;
+        }
+        uint32_t pos[MAXK];
+#pragma unroll
+        for (int a = 0; a < MAXK; ++a)
+            pos[a] = a < k ? (uint32_t)coff[v * (k + 1) + a] + cstart[c * k + a] : 0u;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            uint32_t my = 0;
+#pragma unroll
+            for (int a = 0; a < MAXK; ++a)
+                if (a < k) {
+                    const unsigned m = __ballot_sync(0xffffffffu, cc[r] == a);
+                    if (cc[r] == a) my = pos[a] + __popc(m & lt);
+                    pos[a] += __popc(m);
+                }
+            if (cc[r] >= 0) scol[base + my] = uu[r];
+        }
+    }
+}
+
 // Root-search buckets: X in [0, R) falls in bucket b = floor(X / D), D =
 // ceil(R / nb); start[b] is the first node whose inclusive prefix exceeds
 // b * D, so the node drawn for X lies in [start[b], start[b + 1]].
@@ -548,16 +655,21 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
     const int64_t n = g->n;
     if (n == 0) return;
     // level 1 neighbour sums
-    MC_LAUNCH("gather_h1", s, gather1_kernel<CT><<<grid_for(n, 256), 256, 0, s>>>(g->row_ptr, t->ecol, t->colors, n, k, (CT *)t->S[1]));
-    if (g->n_chunks && k >= 2)
-        MC_LAUNCH("chunk_h1", s, chunk1_kernel<CT><<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
-                                     t->ecol, t->colors, g->chunk_node, g->chunk_e0, g->chunk_e1, g->node_chunk0,
-                                     g->row_ptr, g->n_chunks, k, (CT *)t->Sp[1]));
-    if (g->n_hubs)
-        MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[1], 256), 256, 0, s>>>(
-                                       (const CT *)t->Sp[1], (CT *)t->S[1], g->hub_node, g->hub_chunk0, g->n_hubs,
-                                       G.Ws[1], err));
-
+    // colour blocks of every adjacency list, and the level-1 neighbour sums
+    MC_LAUNCH("colour_blocks", s, colour_blocks_kernel<CT><<<grid_for(n, 256), 256, 0, s>>>(
+                                      g->row_ptr, g->col, t->ecol, t->colors, n, k, t->scol, t->coff,
+                                      (CT *)t->S[1]));
+    if (g->n_hubs) {
+        uint32_t *ccnt = scratch.get<uint32_t>((size_t)g->n_chunks * k);
+        MC_LAUNCH("colour_blocks_hub", s, hub_chunk_counts_kernel<<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
+                                              t->ecol, g->chunk_e0, g->chunk_e1, g->n_chunks, k, ccnt));
+        MC_LAUNCH("colour_blocks_hub", s, hub_chunk_prefix_kernel<CT><<<grid_for(g->n_hubs * 32, 256), 256, 0, s>>>(
+                                              t->colors, g->hub_node, g->hub_chunk0, g->n_hubs, k, ccnt, t->coff,
+                                              (CT *)t->S[1]));
+        MC_LAUNCH("colour_blocks_hub", s, hub_chunk_scatter_kernel<<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
+                                              g->col, t->ecol, g->row_ptr, g->chunk_node, g->chunk_e0, g->chunk_e1,
+                                              g->n_chunks, k, ccnt, t->coff, t->scol));
+    }
     MergeArgs ma{};
     for (int h = 1; h <= k; ++h) {
         ma.c[h] = t->c[h];
@@ -646,9 +758,12 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
             MC_LAUNCH("check_colours", s, check_colours_kernel<<<grid_for(n, 256), 256, 0, s>>>(t->colors, n, k, err));
         }
         t->ecol = t->arena.get<uint8_t>((size_t)g->nnz);
+        t->scol = t->arena.get<uint32_t>((size_t)g->nnz);
+        t->coff = t->arena.get<int32_t>((size_t)n * (k + 1));
         if (g->nnz) {
             MC_LAUNCH("edge_colours", s, edge_colours_kernel<<<grid_for(g->nnz, 256), 256, 0, s>>>(
                                              g->col, t->colors, g->nnz, t->ecol));
+
         }
         // programs
         const Programs &P = programs(k);
@@ -669,7 +784,7 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         // tables
         for (int h = 2; h <= k; ++h) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
         for (int h = 1; h <= k - 1; ++h) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
-        for (int h = 1; h <= k - 1; ++h) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
+        for (int h = 2; h <= k - 1; ++h) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
 
         if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
         else build_levels<u128>(t, err, scratch, s);

@@ -135,6 +135,10 @@ struct mc_tables {
     mc::Geometry geo;
     uint8_t *colors = nullptr;                 // device uint8[n]
     uint8_t *ecol = nullptr;                   // device uint8[nnz]: colour of col[e]
+    uint32_t *scol = nullptr;                  // device uint32[nnz]: each node's neighbours grouped
+                                               // by colour, ascending ids inside a colour
+    int32_t *coff = nullptr;                   // device int32[n*(k+1)]: start of colour a's block in
+                                               // v's row of scol, relative to row_ptr[v]
     void *c[mc::MAXK + 1] = {nullptr};         // level h >= 2: n x Wc[h] counts
     void *S[mc::MAXK + 1] = {nullptr};         // level h <= k-1: n x Ws[h] counts
     void *Sp[mc::MAXK + 1] = {nullptr};        // level h <= k-1: hub chunk partial sums, n_chunks x Ws[h]

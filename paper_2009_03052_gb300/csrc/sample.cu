@@ -295,6 +295,8 @@ struct SampleArgs {
     const uint32_t *col;
     const uint8_t *colors;
     const uint8_t *ecol;
+    const uint32_t *scol;
+    const int32_t *coff;
     int64_t n;
     const void *c[MAXK + 1];
     const void *S[MAXK + 1];
@@ -609,11 +611,17 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             }
             // ---- hub: the 64-neighbour chunk holding the answer, from the
             // chunk partial sums (contiguous per hub and entry)
+            // T'' one node: c(T''_{C''}, u) is 1 for the neighbours of the one
+            // colour of C'' and 0 otherwise, so the answer is the (q+1)-th
+            // neighbour of that colour in ascending id order: position q of
+            // that colour's block in the colour-sorted adjacency
+            const bool single = ok && hb == 1;
+            const bool chunked = ok && !single && chunk0 >= 0;
             const CT *spp = nullptr;
-            if (ok && chunk0 >= 0) spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
+            if (chunked) spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
             int64_t ci = -1;
             CT bc = 0;
-            const bool coop = ok && chunk0 >= 0 && nch > SEQ_CHUNKS;
+            const bool coop = chunked && nch > SEQ_CHUNKS;
             unsigned need = __ballot_sync(FULL, coop);
             while (need) {
                 const int L = __ffs(need) - 1;
@@ -625,11 +633,11 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                 const int64_t cL = warp_first_exceeding<4, CT>(nL, qL, [&](int64_t i) -> CT { return sL[i]; }, bL);
                 if (lane == L) { ci = cL; bc = bL; }
             }
-            if (ok && chunk0 >= 0 && !coop)
+            if (chunked && !coop)
                 ci = lane_first_exceeding<CT>((int)nch, q, [&](int i) -> CT { return spp[i]; }, bc);
             int64_t lo_e = e0, hi_e = e1;
             CT qq = q;
-            if (ok && chunk0 >= 0) {
+            if (chunked) {
                 if (ci < 0) { ok = false; bad = true; }
                 else {
                     lo_e = e0 + ci * HUB_CHUNK;
@@ -639,24 +647,20 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             }
             // ---- neighbour: first u (ascending) whose running sum of
             // c(T''_{C''}, u) exceeds qq (at most HUB_CHUNK neighbours)
-            if (ok) {
+            if (single) {
+                const int col2 = __ffs(C2) - 1;
+                const int32_t b0 = a.coff[(int64_t)x * (a.k + 1) + col2];
+                const int32_t b1 = a.coff[(int64_t)x * (a.k + 1) + col2 + 1];
+                if ((uint64_t)q >= (uint64_t)(b1 - b0) || sp + 2 > MAXK || ne >= MAXK) { ok = false; bad = true; }
+                else {
+                    const uint32_t u = a.scol[e0 + b0 + (int64_t)q];
+                    ea[ne] = x; eb[ne] = u; ++ne;
+                    stg[sp] = gb; stC[sp] = C2; stx[sp] = u; stc[sp] = col2; ++sp;
+                    stg[sp] = ga; stC[sp] = C1; stx[sp] = x; stc[sp] = cx; ++sp;
+                }
+            } else if (ok) {
                 int64_t sel = -1;
-                if (hb == 1) {
-                    // the (qq+1)-th neighbour whose colour is the one colour of C''
-                    const int col2 = __ffs(C2) - 1;
-                    uint64_t rank = (uint64_t)qq;
-                    for (int64_t b = lo_e; b < hi_e && sel < 0; b += 8) {
-                        uint8_t cc[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) cc[i] = b + i < hi_e ? a.ecol[b + i] : (uint8_t)0xff;
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (sel < 0 && cc[i] == col2) {
-                                if (rank == 0) sel = b + i;
-                                else --rank;
-                            }
-                    }
-                } else {
+                {
                     const int lb = a.loc[gb];
                     const CT *chb = (const CT *)a.c[hb];
                     const int bcb = a.Bc[hb], wcb = a.Wc[hb];
@@ -766,6 +770,8 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
     a.col = g->col;
     a.colors = t->colors;
     a.ecol = t->ecol;
+    a.scol = t->scol;
+    a.coff = t->coff;
     a.n = g->n;
     a.node_chunk0 = g->node_chunk0;
     for (int i = 1; i <= t->k; ++i) {
