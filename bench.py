@@ -84,6 +84,21 @@ def algorithmic_bytes(name: str, n: int, nnz: int, k: int, B: int):
 
 
 # ---------------------------------------------------------------------------
+# combining ranks
+# ---------------------------------------------------------------------------
+def job_throughput(units_per_rank: float, my_ms: float, world: int, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank in my_ms; the job took the slowest rank's time.  Returns
+    (max ms over ranks, units of all ranks per second)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([my_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_ms = float(t.item())
+    return my_ms, units_per_rank * world / (my_ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
 class ClockSampler:
@@ -254,20 +269,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         step_ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     launches = M.launch_count() - launches0
-    prof = M.profile_read()
+    prof_b = M.profile_read(with_bytes=True)
+    prof = {k: v[:2] for k, v in prof_b.items()}
     M.profile_enable(False)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    my_total = sum(step_ms)
-    t = torch.tensor([my_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-
     entries = n * live_entries_per_node(k)
-    value = entries * args.steps * world / (total_ms / 1e3)
+    total_ms, value = job_throughput(entries * args.steps, sum(step_ms), world, dist, "cuda")
+    ms_per_step = total_ms / args.steps
     build_ms = statistics.mean(phase["build"])
     sample_ms = statistics.mean(phase["sample"])
 
@@ -281,19 +291,25 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         hbm_peak, peak_src = 6800.0, "fallback"
-    modeled = [(nm, v) for nm, v in prof.items()
-               if algorithmic_bytes(nm, n, nnz, k, BITS // 8) is not None]
-    roof = None
-    if modeled:
-        nm, (ms, cnt) = max(modeled, key=lambda x: x[1][0])
-        by = algorithmic_bytes(nm, n, nnz, k, BITS // 8)
+    def roofline(nm):
+        ms, cnt, counted = prof_b[nm]
+        if counted > 0:
+            by, src = counted / cnt, "counted by the kernel (data items read and written)"
+        else:
+            by = algorithmic_bytes(nm, n, nnz, k, BITS // 8)
+            src = "compulsory bytes (each row read once, written once, plus the CSR)"
+        if by is None:
+            return None
         achieved = by / (ms / cnt / 1e3) / 1e9
-        traffic = TRAFFIC.get((wname, nm))
-        roof = {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": traffic, "algorithmic_bytes": by, "peak_source": peak_src,
-                "avg_launch_ms": round(ms / cnt, 4)}
+        return {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": TRAFFIC.get((wname, nm)), "algorithmic_bytes": int(by),
+                "bytes_model": src, "peak_source": peak_src, "avg_launch_ms": round(ms / cnt, 4)}
+
     top = max(prof.items(), key=lambda x: x[1][0])[0] if prof else None
+    roof = roofline(top) if top else None
+    build_kernels = [nm for nm in prof if nm.startswith(("gather", "merge"))]
+    roof_build = roofline(max(build_kernels, key=lambda x: prof[x][0])) if build_kernels else None
 
     # end to end through the C ABI with host buffers: graph upload, colour,
     # build, sample, estimates copied back
@@ -314,10 +330,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         G2.free()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_t = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = entries * world / (float(e2e_t.item()) / 1e3)
+    _, e2e_value = job_throughput(entries, statistics.median(e2e_ms), world, dist, "cuda")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -344,7 +357,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "samples_per_s": samples * args.steps * world / (total_ms / 1e3),
         "phases_ms": {"build": round(build_ms, 3), "sample_classify_estimate": round(sample_ms, 3)},
         "build_entries_per_s": entries / (build_ms / 1e3),
-        "roofline": roof, "top_kernel": top, "kernels": kernels,
+        "roofline": roof, "roofline_build": roof_build, "top_kernel": top, "kernels": kernels,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.median(e2e_ms),

@@ -226,15 +226,18 @@ mc_status mc_sigma(int h, int64_t *sigma_i, int64_t *sigma_ij);
 /* ------------------------------------------------------------------------ */
 /* When enabled, every kernel the library launches is bracketed by CUDA
  * events recorded on its own stream.  mc_profile_read synchronises those
- * events and reports, per kernel name, the summed device time (ms) and the
- * number of launches: names are written NUL-separated into `names`, at most
- * `max` kernels, their number into *count.  mc_launch_count is the number of
- * kernels launched since the library was loaded, whether or not profiling
- * is on.  Profiling state is process-wide and not thread-safe. */
+ * events and reports, per kernel name, the summed device time (ms), the
+ * number of launches and the bytes of data items the kernel's algorithm
+ * read and wrote, where the kernel counts them (the sampler does, item by
+ * item, while profiling is on; 0 elsewhere): names are written NUL-separated
+ * into `names`, at most `max` kernels, their number into *count; any output
+ * array may be NULL.  mc_launch_count is the number of kernels launched since
+ * the library was loaded, whether or not profiling is on.  Profiling state is
+ * process-wide. */
 mc_status mc_profile_enable(int on);
 mc_status mc_profile_reset(void);
-mc_status mc_profile_read(char *names, size_t names_bytes, double *ms, int64_t *launches, int max,
-                          int *count);
+mc_status mc_profile_read(char *names, size_t names_bytes, double *ms, int64_t *launches, int64_t *bytes,
+                          int max, int *count);
 int64_t mc_launch_count(void);
 
 const char *mc_last_error(void);

@@ -96,7 +96,7 @@ def load(path: str | None = None):
         lib.mc_sigma.argtypes = [C.c_int, P, P]
         lib.mc_last_error.restype = C.c_char_p
         lib.mc_profile_enable.argtypes = [C.c_int]
-        lib.mc_profile_read.argtypes = [P, C.c_size_t, P, P, C.c_int, C.POINTER(C.c_int)]
+        lib.mc_profile_read.argtypes = [P, C.c_size_t, P, P, P, C.c_int, C.POINTER(C.c_int)]
         lib.mc_launch_count.restype = C.c_int64
         lib.mc_estimate_uniform_noalloc.argtypes = [P, C.c_int, u64, u64, i64, P, P, P]
         _lib = lib
@@ -373,19 +373,22 @@ def profile_reset():
     _check(load().mc_profile_reset())
 
 
-def profile_read() -> dict:
-    """{kernel name: (total ms, launches)} of the library's own kernels."""
+def profile_read(with_bytes: bool = False) -> dict:
+    """{kernel name: (total ms, launches[, bytes])} of the library's own
+    kernels; bytes are the counted data bytes of kernels that count them."""
     maxk = 256
     names = C.create_string_buffer(maxk * 32)
     ms = np.zeros(maxk, np.float64)
     launches = np.zeros(maxk, np.int64)
+    nbytes = np.zeros(maxk, np.int64)
     cnt = C.c_int()
-    _check(load().mc_profile_read(names, len(names), _ptr(ms), _ptr(launches), maxk,
+    _check(load().mc_profile_read(names, len(names), _ptr(ms), _ptr(launches), _ptr(nbytes), maxk,
                                   C.byref(cnt)))
     out = {}
     parts = names.raw.split(b"\0")
     for i in range(cnt.value):
-        out[parts[i].decode()] = (float(ms[i]), int(launches[i]))
+        v = (float(ms[i]), int(launches[i]))
+        out[parts[i].decode()] = v + (int(nbytes[i]),) if with_bytes else v
     return out
 
 

@@ -146,6 +146,7 @@ struct ProfState {
     std::vector<std::string> names;
     std::vector<double> ms;
     std::vector<int64_t> launches;
+    std::vector<int64_t> bytes;
     std::vector<std::pair<ProfSpan, int>> pending;
     std::vector<cudaEvent_t> pool;
 };
@@ -197,6 +198,7 @@ ProfSpan prof_begin(const char *name, cudaStream_t s)
         p.names.push_back(name);
         p.ms.push_back(0.0);
         p.launches.push_back(0);
+        p.bytes.push_back(0);
     }
     span.id = id;
     span.a = take_event(p);
@@ -214,6 +216,20 @@ void prof_end(ProfSpan &span, cudaStream_t s)
     p.launches[span.id]++;
     p.pending.emplace_back(span, span.id);
     if (p.pending.size() > 4096) drain(p);
+}
+
+bool prof_enabled() { return prof().on; }
+
+void prof_add_bytes(const char *name, int64_t bytes)
+{
+    ProfState &p = prof();
+    std::lock_guard<std::mutex> lock(p.mu);
+    for (size_t i = 0; i < p.names.size(); ++i)
+        if (p.names[i] == name) { p.bytes[i] += bytes; return; }
+    p.names.push_back(name);
+    p.ms.push_back(0.0);
+    p.launches.push_back(0);
+    p.bytes.push_back(bytes);
 }
 
 int sm_count()
@@ -260,11 +276,12 @@ extern "C" mc_status mc_profile_reset(void)
         drain(p);
         std::fill(p.ms.begin(), p.ms.end(), 0.0);
         std::fill(p.launches.begin(), p.launches.end(), 0);
+        std::fill(p.bytes.begin(), p.bytes.end(), 0);
     });
 }
 
-extern "C" mc_status mc_profile_read(char *names, size_t names_bytes, double *ms, int64_t *launches, int max,
-                                     int *count)
+extern "C" mc_status mc_profile_read(char *names, size_t names_bytes, double *ms, int64_t *launches,
+                                     int64_t *bytes, int max, int *count)
 {
     return guarded([&] {
         ProfState &p = prof();
@@ -281,6 +298,7 @@ extern "C" mc_status mc_profile_read(char *names, size_t names_bytes, double *ms
             }
             if (ms) ms[c] = p.ms[i];
             if (launches) launches[c] = p.launches[i];
+            if (bytes) bytes[c] = p.bytes[i];
             ++c;
         }
         if (count) *count = c;

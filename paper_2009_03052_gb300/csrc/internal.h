@@ -90,6 +90,8 @@ struct ProfSpan {
     cudaEvent_t a = nullptr, b = nullptr;
     int id = -1;
 };
+bool prof_enabled();
+void prof_add_bytes(const char *name, int64_t bytes);
 ProfSpan prof_begin(const char *name, cudaStream_t s);
 void prof_end(ProfSpan &span, cudaStream_t s);
 

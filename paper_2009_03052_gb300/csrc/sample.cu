@@ -320,6 +320,7 @@ struct SampleArgs {
     uint32_t *nodes, *roots;
     int32_t *shapes, *classes;
     unsigned long long *hist;
+    unsigned long long *bytes;  // when set: data bytes read and written, counted item by item
     int ncls;
     int *err;
 };
@@ -456,7 +457,7 @@ __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &befo
 // Up to four adjacency tests at once (binary search of the shorter list),
 // advancing all searches one level per round so their loads overlap.
 __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t *col, const uint32_t *qa,
-                                          const uint32_t *qb, int nq, bool *out)
+                                          const uint32_t *qb, int nq, bool *out, uint64_t &rb)
 {
     int64_t lo[4], hi[4], end[4];
     uint32_t key[4];
@@ -470,6 +471,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             hi[i] = row_ptr[x + 1];
             end[i] = hi[i];
             key[i] = y;
+            rb += 32 + 4;  // both degrees, the final probe
         } else {
             lo[i] = hi[i] = end[i] = 0;
             key[i] = 0;
@@ -483,6 +485,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             if (lo[i] < hi[i]) {
                 const int64_t mid = (lo[i] + hi[i]) >> 1;
                 if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
+                rb += 4;
                 more |= lo[i] < hi[i];
             }
     }
@@ -514,7 +517,9 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int h = a.h;
+    const int CB = (int)sizeof(CT);
     bool bad = false;
+    uint64_t rb = 0;  // bytes of the data items this lane reads and writes
     for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
         const int64_t sid = base + lane;
         const uint64_t index = a.first_index + (uint64_t)sid;
@@ -527,10 +532,13 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
         if (ok) {
             const uint64_t bk = (uint64_t)(X / (V)a.D);
             int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
+            rb += 8;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
+                rb += 16;
             }
+            rb += 32;  // the check below and prefix[v - 1]
             v = (uint32_t)lo;
             if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
         }
@@ -545,6 +553,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             const int found = lane_first_exceeding<V>(a.Wc[h], rem, [&](int e) -> V {
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
+                rb += al ? CB : 0;
                 return al ? (V)vrow[e] : (V)0;
             }, bf);
             if (found < 0) { ok = false; bad = true; }
@@ -578,6 +587,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             CT q = 0;
             if (ok) {
                 ga = a.lft[g]; gb = a.rgt[g]; hb = a.sz[gb];
+                rb += 16 + 4 + CB;  // row offsets, first chunk, c(T_C, x)
                 e0 = a.row_ptr[x];
                 e1 = a.row_ptr[x + 1];
                 chunk0 = a.node_chunk0[x];
@@ -595,6 +605,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                     V before;
                     const int blk = lane_first_exceeding<V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
+                        rb += 2 * CB;
                         return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) *
                                (V)srow[sbase + sm.crank[drop_colour(c2, cx)]];
                     }, before);
@@ -634,7 +645,8 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                 if (lane == L) { ci = cL; bc = bL; }
             }
             if (chunked && !coop)
-                ci = lane_first_exceeding<CT>((int)nch, q, [&](int i) -> CT { return spp[i]; }, bc);
+                ci = lane_first_exceeding<CT>((int)nch, q, [&](int i) -> CT { rb += CB; return spp[i]; }, bc);
+            if (coop) rb += (uint64_t)CB * (uint64_t)(ci + 1);
             int64_t lo_e = e0, hi_e = e1;
             CT qq = q;
             if (chunked) {
@@ -651,6 +663,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                 const int col2 = __ffs(C2) - 1;
                 const int32_t b0 = a.coff[(int64_t)x * (a.k + 1) + col2];
                 const int32_t b1 = a.coff[(int64_t)x * (a.k + 1) + col2 + 1];
+                rb += 8 + 4;
                 if ((uint64_t)q >= (uint64_t)(b1 - b0) || sp + 2 > MAXK || ne >= MAXK) { ok = false; bad = true; }
                 else {
                     const uint32_t u = a.scol[e0 + b0 + (int64_t)q];
@@ -667,7 +680,9 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                     CT bn;
                     const int r = lane_first_exceeding<CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
+                        rb += 1;
                         if (!((C2 >> cu) & 1u)) return (CT)0;
+                        rb += 4 + CB;
                         const uint32_t u = a.col[lo_e + i];
                         return chb[(int64_t)u * wcb + lb * bcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)]];
                     }, bn);
@@ -716,7 +731,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                 qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
                 if (nq == 4 || p == P - 1) {
                     bool r4[4];
-                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4);
+                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
                     for (int t = 0; t < nq; ++t)
                         if (r4[t]) word |= 1u << qp[t];
                     nq = 0;
@@ -724,20 +739,27 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             }
             if (nq) {
                 bool r4[4];
-                adjacent4(a.row_ptr, a.col, qa, qb, nq, r4);
+                adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
                 for (int t = 0; t < nq; ++t)
                     if (r4[t]) word |= 1u << qp[t];
             }
             cls = a.lut[word];
+            rb += 2;
             if (cls == 0xffff) { cls = -1; bad = true; }
             if (a.nodes) for (int i = 0; i < h; ++i) a.nodes[sid * h + i] = nodes[i];
             if (a.roots) a.roots[sid] = v;
             if (a.shapes) a.shapes[sid] = s0;
+            rb += (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
             if (a.hist && cls >= 0) atomicAdd(&s_hist[cls], 1u);
         }
         if (sid < a.count && a.classes) a.classes[sid] = cls;
     }
     if (bad) atomicOr(a.err, SERR_SEARCH);
+    if (a.bytes) {
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) rb += __shfl_xor_sync(0xffffffffu, rb, d);
+        if (lane == 0) atomicAdd(a.bytes, (unsigned long long)rb);
+    }
     if (a.hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < a.ncls; i += blockDim.x)
@@ -872,6 +894,26 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     MC_LAUNCH("sample", s, kern<<<(unsigned)grid, block, smem, s>>>(a));
 }
 
+// While profiling is on, the sampler counts the bytes of the data items it
+// reads and writes into a device counter from `scratch`; the count is added
+// to the profile after the launch (one more synchronisation).
+static unsigned long long *sample_byte_counter(Arena &scratch, cudaStream_t s)
+{
+    if (!prof_enabled()) return nullptr;
+    unsigned long long *c = scratch.get<unsigned long long>(1);
+    MC_CUDA(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
+    return c;
+}
+
+static void report_sample_bytes(const unsigned long long *c, cudaStream_t s)
+{
+    if (!c) return;
+    unsigned long long v = 0;
+    MC_CUDA(cudaMemcpyAsync(&v, c, sizeof(v), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    prof_add_bytes("sample", (int64_t)v);
+}
+
 static double inv_colourful_prob(int k, int h)
 {
     double num = 1.0, den = 1.0;
@@ -975,7 +1017,9 @@ extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape
         a.hist = nullptr;
         a.ncls = (int)cc->codes.size();
         a.err = err;
+        a.bytes = sample_byte_counter(scratch, s);
         launch_sampler(t, a, s);
+        report_sample_bytes(a.bytes, s);
         int herr[2] = {0, 0};
         MC_CUDA(cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
         MC_CUDA(cudaStreamSynchronize(s));
@@ -1025,7 +1069,9 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             a.hist = dh;
             a.ncls = ncls;
             a.err = err;
+            a.bytes = sample_byte_counter(scratch, s);
             launch_sampler(t, a, s);
+            report_sample_bytes(a.bytes, s);
             MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, ri.R / (u128)h, p->samples, ip, dest));
             std::vector<unsigned long long> hh((size_t)ncls);
             MC_CUDA(cudaMemcpyAsync(hh.data(), dh, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
@@ -1100,7 +1146,9 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.classes = dcls;
                 a.ncls = ncls;
                 a.err = err;
+                a.bytes = sample_byte_counter(scratch, s);
                 launch_sampler(t, a, s);
+                report_sample_bytes(a.bytes, s);
                 MC_CUDA(cudaMemcpyAsync(hcls.data(), dcls, (size_t)b * 4, cudaMemcpyDeviceToHost, s));
                 MC_CUDA(cudaStreamSynchronize(s));
                 st.batches++;
