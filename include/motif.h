@@ -96,9 +96,16 @@ mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, voi
  * S(T'', C'', v) = sum_{u ~ v} c(T''_{C''}, u) and the disjoint-colour merge
  * c(T_C, v) = (1/beta_T) sum_{C' + C'' = C} c(T'_{C'}, v) S(T'', C'', v).
  * colors: device uint8[n] with values < k (read during the call only).
- * count_bits: 64 or 128.  flags: 0 (reserved).  The tables stay on the device
+ * count_bits: 64 or 128.  flags: 0 or MC_BUILD_ZERO_ROOT.  The tables stay on the device
  * until mc_free_tables; they are immutable, so concurrent readers are safe.
  * The graph must outlive the tables. */
+/* Zero-rooting (Section 3.4.1): keep the level-k counts only at nodes of
+ * colour 0 (zero elsewhere).  Every colourful k-treelet has exactly one
+ * colour-0 node, so level k then holds each copy once: its total is t itself
+ * (not h t), and sampling at h = k draws the root among colour-0 nodes, still
+ * uniformly over the copies. */
+#define MC_BUILD_ZERO_ROOT 0x1u
+
 mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
                           uint32_t flags, const mc_allocator *alloc, void *stream,
                           mc_tables **out);
@@ -106,9 +113,10 @@ void mc_free_tables(mc_tables *t);
 
 /* Totals (the occ() queries of Section 3): rooted = sum over v and over the
  * rooted shapes of size h (all of them when unrooted_shape < 0, else the
- * rootings of that unrooted shape) of c(T_C, v); unrooted = rooted / h, the
- * number of colourful h-treelet copies t (or t_j).  Host uint64[2] each,
- * low word first.  Synchronises `stream`. */
+ * rootings of that unrooted shape) of the stored c(T_C, v); unrooted = the
+ * number of colourful h-treelet copies t (or t_j): rooted / h, or rooted
+ * itself for a zero-rooted level k.  Host uint64[2] each, low word first.
+ * Synchronises `stream`. */
 mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
                    uint64_t unrooted_count[2], void *stream);
 

@@ -74,7 +74,7 @@ def _load():
         lib.oc_draw_below.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, u64p, u64p]
         lib.oc_build.restype = P
         lib.oc_build.argtypes = [C.c_int64, i64p, u32p, u8p, C.c_int, C.c_int, C.c_int,
-                                 i32p, i32p, i32p, i32p, i32p, i32p, C.c_int,
+                                 i32p, i32p, i32p, i32p, i32p, i32p, C.c_int, C.c_int,
                                  C.POINTER(C.c_int)]
         lib.oc_free.argtypes = [P]
         lib.oc_read_level.argtypes = [P, C.c_int, u64p]
@@ -201,9 +201,10 @@ def inv_colorful_prob(k: int, h: int) -> float:
 class Tables:
     """Exact count tables c(T_C, v) for |T| = 1..k (Section 2.1, Eq. 1)."""
 
-    def __init__(self, graph, colors, k: int, width: int = 128, nthreads: int | None = None):
+    def __init__(self, graph, colors, k: int, width: int = 128, nthreads: int | None = None,
+                 zero_root: bool = False):
         lib = _load()
-        self.k, self.width = k, width
+        self.k, self.width, self.zero_root = k, width, zero_root
         self.n = int(graph.n)
         self.cat = _cat.Catalog(k)
         nsh, *arrs = _catalog_arrays(self.cat)
@@ -216,7 +217,8 @@ class Tables:
         self.nthreads = nthreads
         h = lib.oc_build(self.n, np.ascontiguousarray(graph.row_ptr, np.int64),
                          np.ascontiguousarray(graph.col, np.uint32), colors if self.n else
-                         np.zeros(1, np.uint8), k, width, nsh, *arrs, nthreads, C.byref(st))
+                         np.zeros(1, np.uint8), k, width, nsh, *arrs, nthreads,
+                         1 if zero_root else 0, C.byref(st))
         _check(st.value, "build")
         self._h = h
 

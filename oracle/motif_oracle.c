@@ -98,6 +98,7 @@ typedef struct {
     uint32_t *col;
     uint8_t *colors;
     int k, width;                 /* width: 64 or 128 */
+    int zero_root;                /* level k stored at colour-0 nodes only (Section 3.4.1) */
     int nshape;
     int32_t *size, *local, *left, *right, *beta, *unrooted;
     int first[MAXK + 2];          /* global id of the first shape of size h */
@@ -163,6 +164,9 @@ static void *build_level_worker(void *arg)
     const int h = job->h;
     for (int64_t v = job->tid; v < t->n; v += t->nthreads) {
         const unsigned cv = 1u << t->colors[v];
+        /* Zero-rooting (Section 3.4.1): level-k counts are kept only at nodes
+         * of colour 0; every colourful k-treelet has exactly one such node. */
+        if (t->zero_root && h == t->k && t->colors[v] != 0) continue;
         for (int g = t->first[h]; g < t->first[h + 1]; ++g) {
             const int a = t->left[g], b = t->right[g];
             const int ha = t->size[a];
@@ -251,13 +255,13 @@ static int binom(int n, int r)
 oc_tables *oc_build(int64_t n, const int64_t *row_ptr, const uint32_t *col, const uint8_t *colors,
                     int k, int width, int nshape, const int32_t *size, const int32_t *local,
                     const int32_t *left, const int32_t *right, const int32_t *beta,
-                    const int32_t *unrooted, int nthreads, int *status)
+                    const int32_t *unrooted, int nthreads, int zero_root, int *status)
 {
     *status = OC_INVALID;
     if (k < 1 || k > MAXK || (width != 64 && width != 128) || n < 0) return NULL;
     oc_tables *t = (oc_tables *)calloc(1, sizeof(oc_tables));
     if (!t) { *status = OC_NOMEM; return NULL; }
-    t->n = n; t->k = k; t->width = width; t->nshape = nshape;
+    t->n = n; t->k = k; t->width = width; t->nshape = nshape; t->zero_root = zero_root != 0;
     t->nthreads = nthreads < 1 ? 1 : nthreads;
     t->nnz = row_ptr[n];
     t->row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
@@ -348,15 +352,18 @@ static u128 node_total(const oc_tables *t, int h, int unrooted, int64_t v)
 }
 
 /* Rooted total R = sum_v sum_{T, C} c(T_C, v) over the shapes of size h (all,
- * or the rootings of one unrooted shape); the unrooted count is R / h. */
+ * or the rootings of one unrooted shape); the unrooted count is R / h, each
+ * copy having h rootings -- or R itself for a zero-rooted level k, where
+ * each copy is stored once, at its colour-0 node. */
 int oc_total(const oc_tables *t, int h, int unrooted, uint64_t rooted[2], uint64_t unrooted_count[2])
 {
     if (h < 1 || h > t->k) return OC_INVALID;
     u128 R = 0;
     for (int64_t v = 0; v < t->n; ++v)
         if (__builtin_add_overflow(R, node_total(t, h, unrooted, v), &R)) return OC_OVERFLOW;
-    if (R % (u128)h != 0) return OC_INTERNAL;
-    u128 U = R / (u128)h;
+    const u128 div = (t->zero_root && h == t->k) ? 1 : (u128)h;
+    if (R % div != 0) return OC_INTERNAL;
+    u128 U = R / div;
     rooted[0] = (uint64_t)R; rooted[1] = (uint64_t)(R >> 64);
     unrooted_count[0] = (uint64_t)U; unrooted_count[1] = (uint64_t)(U >> 64);
     return OC_OK;
@@ -721,7 +728,7 @@ static void *sigma_worker(void *arg)
         for (int i = 0; i < h; ++i) colors[i] = (uint8_t)i;
         int st;
         oc_tables *t = oc_build(h, row_ptr, col, colors, h, 128, jb->nshape, jb->size, jb->local,
-                                jb->left, jb->right, jb->beta, jb->unrooted, 1, &st);
+                                jb->left, jb->right, jb->beta, jb->unrooted, 1, 0, &st);
         if (!t) { jb->status = st; return NULL; }
         for (int j = 0; j < jb->n_unrooted; ++j) {
             uint64_t R[2], U[2];

@@ -24,6 +24,7 @@ MC_OK, MC_E_INVALID, MC_E_NOMEM, MC_E_OVERFLOW, MC_E_CUDA, MC_E_TIMEOUT, MC_E_UN
     MC_E_INTERNAL = range(8)
 MC_GRAPH_DEVICE_PTRS = 1
 MC_GRAPH_TRUSTED = 2
+MC_BUILD_ZERO_ROOT = 1
 MC_EST_UNIFORM = 0
 MC_EST_AGS = 1
 
@@ -232,7 +233,8 @@ def color(graph: Graph, k: int, seed: int, out=None, stream=None):
 class Tables:
     """mc_build_tables: the exact colourful treelet count tables."""
 
-    def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None):
+    def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None,
+                 zero_root: bool = False):
         torch = _torch()
         if not (hasattr(colors, "is_cuda") and colors.is_cuda):
             colors = torch.as_tensor(np.ascontiguousarray(colors, dtype=np.uint8)).cuda()
@@ -240,7 +242,8 @@ class Tables:
         self._alloc = torch_allocator()
         h = C.c_void_p()
         _check(load().mc_build_tables(graph.handle, _ptr(colors) if graph.n else None, k,
-                                      count_bits, 0, C.byref(self._alloc.struct),
+                                      count_bits, MC_BUILD_ZERO_ROOT if zero_root else 0,
+                                      C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
 

@@ -184,6 +184,7 @@ struct MergeArgs {
     void *out;
     int64_t n;
     int W;
+    const uint8_t *zero_root_colors;  // set: only colour-0 nodes get counts
     int *err;
 };
 
@@ -196,6 +197,10 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = t / a.W;
         const int o = (int)(t - v * a.W);
+        if (a.zero_root_colors && a.zero_root_colors[v] != 0) {
+            ((CT *)a.out)[t] = 0;
+            continue;
+        }
         const int info = a.info[o];
         const int h1 = info & 15, h2 = (info >> 4) & 15, beta = (info >> 8) & 255, nt = info >> 16;
         const uint32_t *term = a.terms + a.off[o];
@@ -686,6 +691,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
         ma.terms = t->m_terms[h];
         ma.out = t->c[h];
         ma.W = G.Wc[h];
+        ma.zero_root_colors = (t->zero_root && h == k) ? t->colors : nullptr;
         MC_LAUNCH(kMergeName[h], s, merge_kernel<CT><<<grid_for(n * G.Wc[h], 256), 256, 0, s>>>(ma));
         if (h <= k - 1) {
             GatherArgs ga{};
@@ -735,12 +741,13 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         MC_REQUIRE(colors || g->n == 0, "colors is NULL");
         if (k < 2 || k > MAXK) throw Error(MC_E_UNSUPPORTED, "k must be in 2..8");
         MC_REQUIRE(count_bits == 64 || count_bits == 128, "count_bits must be 64 or 128");
-        MC_REQUIRE(flags == 0, "unknown flags");
+        MC_REQUIRE((flags & ~MC_BUILD_ZERO_ROOT) == 0, "unknown flags");
         cudaStream_t s = (cudaStream_t)stream;
         t = new mc_tables();
         t->g = g;
         t->k = k;
         t->bits = count_bits;
+        t->zero_root = flags & MC_BUILD_ZERO_ROOT;
         t->geo = make_geometry(k);
         t->arena.stream = s;
         if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
@@ -885,8 +892,9 @@ extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape,
             MC_CUDA(cudaStreamSynchronize(s));
             if (herr) throw Error(MC_E_OVERFLOW, "level total does not fit in 128 bits");
         }
-        if (R % (u128)h != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
-        const u128 U = R / (u128)h;
+        const u128 div = (u128)t->copies_div(h);
+        if (R % div != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
+        const u128 U = R / div;
         rooted[0] = (uint64_t)R;
         rooted[1] = (uint64_t)(R >> 64);
         unrooted_count[0] = (uint64_t)U;

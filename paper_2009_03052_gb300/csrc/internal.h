@@ -134,6 +134,9 @@ struct mc_graph {
 struct mc_tables {
     const mc_graph *g = nullptr;
     int k = 0, bits = 64;
+    bool zero_root = false;  // level k stored at colour-0 nodes only
+    // copies per stored level-h entry sum: h, or 1 for a zero-rooted level k
+    int copies_div(int h) const { return (zero_root && h == k) ? 1 : h; }
     mc::Geometry geo;
     uint8_t *colors = nullptr;                 // device uint8[n]
     uint8_t *ecol = nullptr;                   // device uint8[nnz]: colour of col[e]

@@ -1072,7 +1072,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             a.bytes = sample_byte_counter(scratch, s);
             launch_sampler(t, a, s);
             report_sample_bytes(a.bytes, s);
-            MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, ri.R / (u128)h, p->samples, ip, dest));
+            MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, ri.R / (u128)t->copies_div(h), p->samples, ip, dest));
             std::vector<unsigned long long> hh((size_t)ncls);
             MC_CUDA(cudaMemcpyAsync(hh.data(), dh, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
             MC_CUDA(cudaMemcpyAsync(est, dest, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
@@ -1297,7 +1297,7 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         launch_sampler(t, a, s);
         const double ip = inv_colourful_prob(t->k, h);
         MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(
-                                     scr->hist, scr->sigma, ncls, t->R[h] / (u128)h, samples, ip, scr->est));
+                                     scr->hist, scr->sigma, ncls, t->R[h] / (u128)t->copies_div(h), samples, ip, scr->est));
         int herr[2] = {0, 0};
         MC_CUDA(cudaMemcpyAsync(hits, scr->hist, (size_t)ncls * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         MC_CUDA(cudaMemcpyAsync(est, scr->est, (size_t)ncls * sizeof(double), cudaMemcpyDeviceToHost, s));

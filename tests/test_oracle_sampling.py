@@ -66,6 +66,24 @@ def test_sampler_is_uniform_over_colourful_treelets(oracle, k, seed):
     assert _chi2_ok(obs, exact, total, N)
 
 
+def test_zero_rooted_sampler_is_uniform(oracle):
+    # with zero-rooting the root is each copy's colour-0 node; every colourful
+    # k-treelet copy must still come up with probability 1/t
+    k = 4
+    g = synth.erdos_renyi(10, 4.5, seed=12)
+    colors = synth.balanced_colors(g.n, k, seed=12)
+    T = oracle.Tables(g, colors, k, 64, nthreads=1, zero_root=True)
+    exact, total = _exact_outcomes(g, colors, k)
+    exact = Counter({key: c for key, c in exact.items() if colors[key[1]] == 0})
+    total = sum(exact.values())
+    assert total == T.total(k)[0] == T.total(k)[1]
+    N = 40 * len(exact) + 4000
+    nodes, roots, shapes, _ = T.sample(k, seed=3, first_index=0, count=N)
+    obs = Counter((tuple(int(x) for x in nodes[i]), int(roots[i]), int(shapes[i]))
+                  for i in range(N))
+    assert _chi2_ok(obs, exact, total, N)
+
+
 def test_sampler_restricted_to_one_shape(oracle):
     k = 4
     g = synth.erdos_renyi(10, 4.5, seed=4)

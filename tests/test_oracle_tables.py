@@ -175,3 +175,21 @@ def test_neighbor_sum_definition(oracle):
             S = T.neighbor_sum(h, v)
             want = sum(lv[int(u), :, :, 0] for u in g.neighbors(v))
             assert (S[:, :, 0].astype(object) == want).all()
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_zero_rooting_keeps_each_copy_once(oracle, k):
+    # Section 3.4.1: level-k counts only at colour-0 nodes.  Every colourful
+    # k-treelet has exactly one colour-0 node, so the zero-rooted level k holds
+    # each copy once: its total is t (= rooted total / k of the full table).
+    for gi, g in enumerate([synth.erdos_renyi(40, 5.0, seed=k), synth.chung_lu(300, 1500, 2.4, seed=k)]):
+        colors = synth.random_colors(g.n, k, seed=gi)
+        A = oracle.Tables(g, colors, k, 128)
+        Z = oracle.Tables(g, colors, k, 128, zero_root=True)
+        for j in range(len(cat.unrooted_shapes(k))):
+            assert Z.total(k, j) == (A.total(k, j)[1], A.total(k, j)[1])
+        la, lz = A.level(k), Z.level(k)
+        zero = colors == 0
+        assert np.array_equal(la[zero], lz[zero]) and not lz[~zero].any()
+        for h in range(1, k):
+            assert np.array_equal(A.level(h), Z.level(h))
