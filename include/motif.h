@@ -119,6 +119,24 @@ void mc_free_tables(mc_tables *t);
  * Synchronises `stream`. */
 mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
                    uint64_t unrooted_count[2], void *stream);
+/* The same over the treelets rooted at nodes [node_lo, node_hi) (node_hi <= 0:
+ * to the last node), e.g. one instance of a batch. */
+mc_status mc_total_range(const mc_tables *t, int h, int32_t unrooted_shape, int64_t node_lo, int64_t node_hi,
+                         uint64_t rooted[2], uint64_t unrooted_count[2], void *stream);
+
+/* Batches (many colourings of one graph, many graphs): build the tables of
+ * `count` independent (graph, colouring) instances in one pass.  The
+ * instances are laid side by side as one disjoint union, so every kernel of
+ * the build is launched once for the whole batch; instance i owns the union's
+ * nodes [node_offsets[i], node_offsets[i+1]) (host int64[count+1], written),
+ * its node v being union node node_offsets[i] + v with the same neighbour
+ * order.  Treelets never cross instances, so every count, total and sample
+ * of instance i (queried with its node range) equals that of its own
+ * mc_build_tables, with node ids shifted by node_offsets[i].  The graphs and
+ * colour buffers are read during the call only. */
+mc_status mc_build_tables_batch(int count, const mc_graph *const *graphs, const uint8_t *const *colors, int k,
+                                int count_bits, uint32_t flags, const mc_allocator *alloc, void *stream,
+                                mc_tables **out, int64_t *node_offsets);
 
 /* Layout of the level-h table (which = 0: counts c, h = 1..k; which = 1:
  * neighbour sums S, h = 1..k-1).  Row v holds row_entries entries of
@@ -150,6 +168,12 @@ mc_status mc_read_table(const mc_tables *t, int h, int which, void *dst, size_t 
 mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
                     uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
                     int32_t *shapes, int32_t *classes, void *stream);
+/* The same restricted to the treelets rooted at nodes [node_lo, node_hi) --
+ * for a batch instance, exactly its own samples (node ids in the union's
+ * numbering). */
+mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted_shape, int64_t node_lo, int64_t node_hi,
+                          uint64_t seed, uint64_t first_index, int64_t count, uint32_t *nodes,
+                          uint32_t *roots, int32_t *shapes, int32_t *classes, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Estimation (Section 2.2 uniform; Algorithm AGS, Section 4.1)              */
@@ -166,6 +190,7 @@ typedef struct {
     int64_t cbar;          /* AGS covering threshold; <= 0: ceil(4/eps^2 ln(2s/delta)) */
     double eps, delta;     /* AGS accuracy, used when cbar <= 0 */
     int64_t batch;         /* AGS speculative batch; <= 0: automatic */
+    int64_t node_lo, node_hi;  /* root nodes [node_lo, node_hi); node_hi <= 0: all nodes */
 } mc_estimate_params;
 
 typedef struct {

@@ -33,7 +33,8 @@ EXPORTED = [
     "mc_free_tables", "mc_total", "mc_table_layout", "mc_read_table", "mc_sample",
     "mc_estimate_counts", "mc_num_shapes", "mc_num_unrooted", "mc_num_classes", "mc_shape_info",
     "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
-    "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc",
+    "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
+    "mc_sample_range", "mc_build_tables_batch",
 ]
 
 
@@ -56,7 +57,8 @@ class Allocator(C.Structure):
 class EstimateParams(C.Structure):
     _fields_ = [("mode", C.c_int), ("h", C.c_int), ("seed", C.c_uint64),
                 ("first_index", C.c_uint64), ("samples", C.c_int64), ("cbar", C.c_int64),
-                ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64)]
+                ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64),
+                ("node_lo", C.c_int64), ("node_hi", C.c_int64)]
 
 
 class EstimateStats(C.Structure):
@@ -85,6 +87,10 @@ def load(path: str | None = None):
         lib.mc_free_tables.argtypes = [P]
         lib.mc_free_tables.restype = None
         lib.mc_total.argtypes = [P, C.c_int, i32, P, P, P]
+        lib.mc_total_range.argtypes = [P, C.c_int, i32, i64, i64, P, P, P]
+        lib.mc_sample_range.argtypes = [P, C.c_int, i32, i64, i64, u64, u64, i64, P, P, P, P, P]
+        lib.mc_build_tables_batch.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_uint32, P, P,
+                                              C.POINTER(P), P]
         lib.mc_table_layout.argtypes = [P, C.c_int, C.c_int, C.POINTER(i64), C.POINTER(C.c_int)]
         lib.mc_read_table.argtypes = [P, C.c_int, C.c_int, P, C.c_size_t, C.c_int, P]
         lib.mc_sample.argtypes = [P, C.c_int, i32, u64, u64, i64, P, P, P, P, P]
@@ -234,8 +240,12 @@ class Tables:
     """mc_build_tables: the exact colourful treelet count tables."""
 
     def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None,
-                 zero_root: bool = False):
+                 zero_root: bool = False, _handle=None):
         torch = _torch()
+        if _handle is not None:  # built by batch()
+            self.graph, self.k, self.bits, self._alloc, self.handle = graph, k, count_bits, \
+                torch_allocator(), _handle
+            return
         if not (hasattr(colors, "is_cuda") and colors.is_cuda):
             colors = torch.as_tensor(np.ascontiguousarray(colors, dtype=np.uint8)).cuda()
         self.graph, self.k, self.bits = graph, k, count_bits
@@ -246,6 +256,29 @@ class Tables:
                                       C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
+
+    @classmethod
+    def batch(cls, graphs, colors, k: int, count_bits: int = 64, zero_root: bool = False,
+              stream=None):
+        """mc_build_tables_batch: one build over the disjoint union of the
+        instances; returns (tables, node offsets) -- instance i owns union
+        nodes [offsets[i], offsets[i+1])."""
+        torch = _torch()
+        cols = [c if (hasattr(c, "is_cuda") and c.is_cuda) else
+                torch.as_tensor(np.ascontiguousarray(c, dtype=np.uint8)).cuda() for c in colors]
+        gh = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+        ch = (C.c_void_p * len(cols))(*[_ptr(c) for c in cols])
+        offs = np.zeros(len(graphs) + 1, np.int64)
+        alloc = torch_allocator()
+        h = C.c_void_p()
+        _check(load().mc_build_tables_batch(len(graphs), gh, ch, k, count_bits,
+                                            MC_BUILD_ZERO_ROOT if zero_root else 0,
+                                            C.byref(alloc.struct), _stream_ptr(stream), C.byref(h),
+                                            _ptr(offs)))
+
+        class _Union:  # the union graph is owned by the tables
+            n = int(offs[-1])
+        return cls(_Union(), None, k, count_bits, _handle=h), offs
 
     def free(self):
         if getattr(self, "handle", None):
@@ -258,11 +291,13 @@ class Tables:
         except Exception:
             pass
 
-    def total(self, h: int, unrooted: int = -1, stream=None) -> tuple[int, int]:
-        """mc_total: (rooted total, number of colourful h-treelet copies)."""
+    def total(self, h: int, unrooted: int = -1, node_range=(0, 0), stream=None) -> tuple[int, int]:
+        """mc_total_range: (rooted total, number of colourful h-treelet
+        copies), over the roots in node_range ((0, 0): all nodes)."""
         r = np.zeros(2, np.uint64)
         u = np.zeros(2, np.uint64)
-        _check(load().mc_total(self.handle, h, unrooted, _ptr(r), _ptr(u), _stream_ptr(stream)))
+        _check(load().mc_total_range(self.handle, h, unrooted, node_range[0], node_range[1],
+                                     _ptr(r), _ptr(u), _stream_ptr(stream)))
         return _u128(r), _u128(u)
 
     def layout(self, h: int, which: int = 0) -> tuple[int, int]:
@@ -281,7 +316,7 @@ class Tables:
         return out[: self.graph.n * W * words].reshape(self.graph.n, W, words)
 
     def sample(self, h: int, seed: int, first_index: int, count: int, unrooted: int = -1,
-               nodes=True, roots=True, shapes=True, classes=True, stream=None):
+               nodes=True, roots=True, shapes=True, classes=True, node_range=(0, 0), stream=None):
         """mc_sample: device tensors (nodes [count, h], roots, shapes, classes)."""
         torch = _torch()
         dev = "cuda"
@@ -290,19 +325,21 @@ class Tables:
         t_shapes = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if shapes else None
         t_cls = torch.empty(max(count, 1), dtype=torch.int32, device=dev) if classes else None
         p = lambda t: _ptr(t) if t is not None else None
-        _check(load().mc_sample(self.handle, h, unrooted, seed, first_index, count, p(t_nodes),
-                                p(t_roots), p(t_shapes), p(t_cls), _stream_ptr(stream)))
+        _check(load().mc_sample_range(self.handle, h, unrooted, node_range[0], node_range[1], seed,
+                                      first_index, count, p(t_nodes), p(t_roots), p(t_shapes),
+                                      p(t_cls), _stream_ptr(stream)))
         cut = lambda t: t[:count] if t is not None else None
         return cut(t_nodes), cut(t_roots), cut(t_shapes), cut(t_cls)
 
     def estimate(self, h: int, seed: int, samples: int, mode: int = MC_EST_UNIFORM,
                  first_index: int = 0, cbar: int = 0, eps: float = 0.0, delta: float = 0.0,
-                 batch: int = 0, stream=None):
+                 batch: int = 0, node_range=(0, 0), stream=None):
         """mc_estimate_counts: (estimates, hits, stats dict)."""
         ncls = num_classes(h)
         est = np.zeros(ncls, np.float64)
         hits = np.zeros(ncls, np.uint64)
-        prm = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch)
+        prm = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
+                             node_range[0], node_range[1])
         st = EstimateStats()
         _check(load().mc_estimate_counts(self.handle, C.byref(prm), _ptr(est), _ptr(hits),
                                          C.byref(st), _stream_ptr(stream)))

@@ -854,43 +854,62 @@ void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
     t->prefix[h] = p;  // published last
 }
 
-extern "C" void mc_free_tables(mc_tables *t) { delete t; }
+extern "C" void mc_free_tables(mc_tables *t)
+{
+    if (!t) return;
+    mc_graph *owned = t->owned_graph;
+    delete t;
+    mc_free_graph(owned);
+}
 
-extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
-                              uint64_t unrooted_count[2], void *stream)
+extern "C" mc_status mc_total_range(const mc_tables *t, int h, int32_t unrooted_shape, int64_t node_lo,
+                                    int64_t node_hi, uint64_t rooted[2], uint64_t unrooted_count[2], void *stream)
 {
     return guarded([&] {
         MC_REQUIRE(t && rooted && unrooted_count, "NULL argument");
         MC_REQUIRE(h >= 1 && h <= t->k, "h must be in 1..k");
         const ShapeCatalog &cat = shape_catalog();
         MC_REQUIRE(unrooted_shape < cat.n_unrooted[h], "unrooted shape out of range");
+        const int64_t n = t->g->n;
+        int64_t lo = node_lo, hi = node_hi;
+        if (hi <= 0 && lo <= 0) { lo = 0; hi = n; }
+        if (hi <= 0) hi = n;
+        MC_REQUIRE(lo >= 0 && lo <= hi && hi <= n, "node range out of bounds");
+        cudaStream_t s = (cudaStream_t)stream;
         u128 R = 0;
         if (h == 1) {
-            R = (u128)t->g->n;
-            if (unrooted_shape > 0) R = 0;
-        } else if (unrooted_shape < 0) {
-            ensure_level_index(t, h, (cudaStream_t)stream);
-            R = t->R[h];
-        } else if (t->g->n > 0) {
-            cudaStream_t s = (cudaStream_t)stream;
-            uint64_t a0 = 0, a1 = 0;
-            for (int i = 0; i < cat.r[h]; ++i)
-                if (cat.shapes[cat.gid(h, i)].unrooted == unrooted_shape) {
-                    if (i < 64) a0 |= 1ull << i; else a1 |= 1ull << (i - 64);
-                }
+            R = unrooted_shape > 0 ? 0 : (u128)(hi - lo);
+        } else if (hi > lo) {
+            // the level's node prefix (all shapes: the cached root index; one
+            // unrooted shape: computed here), read at the range's ends
+            const u128 *pre = nullptr;
             Arena scratch;
             scratch.alloc = t->arena.alloc;
             scratch.stream = s;
             int *err = scratch.get<int>(1);
             MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-            u128 *tot = scratch.get<u128>((size_t)t->g->n);
-            launch_row_totals(t, h, a0, a1, tot, err, s);
-            inclusive_scan_u128(tot, t->g->n, err, scratch, s);
+            if (unrooted_shape < 0) {
+                ensure_level_index(t, h, s);
+                pre = t->prefix[h];
+            } else {
+                uint64_t a0 = 0, a1 = 0;
+                for (int i = 0; i < cat.r[h]; ++i)
+                    if (cat.shapes[cat.gid(h, i)].unrooted == unrooted_shape) {
+                        if (i < 64) a0 |= 1ull << i; else a1 |= 1ull << (i - 64);
+                    }
+                u128 *tot = scratch.get<u128>((size_t)n);
+                launch_row_totals(t, h, a0, a1, tot, err, s);
+                inclusive_scan_u128(tot, n, err, scratch, s);
+                pre = tot;
+            }
+            u128 top = 0, base = 0;
             int herr = 0;
-            MC_CUDA(cudaMemcpyAsync(&R, tot + (t->g->n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(&top, pre + (hi - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            if (lo > 0) MC_CUDA(cudaMemcpyAsync(&base, pre + (lo - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
             MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             MC_CUDA(cudaStreamSynchronize(s));
             if (herr) throw Error(MC_E_OVERFLOW, "level total does not fit in 128 bits");
+            R = top - base;
         }
         const u128 div = (u128)t->copies_div(h);
         if (R % div != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
@@ -900,6 +919,76 @@ extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape,
         unrooted_count[0] = (uint64_t)U;
         unrooted_count[1] = (uint64_t)(U >> 64);
     });
+}
+
+extern "C" mc_status mc_total(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t rooted[2],
+                              uint64_t unrooted_count[2], void *stream)
+{
+    return mc_total_range(t, h, unrooted_shape, 0, 0, rooted, unrooted_count, stream);
+}
+
+// ---------------------------------------------------------------------------
+// batches: several (graph, colouring) instances side by side as one disjoint
+// union, built in one pass (one launch per kernel for the whole batch)
+// ---------------------------------------------------------------------------
+__global__ void concat_csr_kernel(const int64_t *__restrict__ rp, const uint32_t *__restrict__ col, int64_t n,
+                                  int64_t nnz, int64_t noff, int64_t eoff, int64_t *__restrict__ urp,
+                                  uint32_t *__restrict__ ucol)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz || i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) urp[noff + i] = eoff + rp[i];
+        if (i < nnz) ucol[eoff + i] = col[i] + (uint32_t)noff;
+    }
+}
+
+extern "C" mc_status mc_build_tables_batch(int count, const mc_graph *const *graphs, const uint8_t *const *colors,
+                                           int k, int count_bits, uint32_t flags, const mc_allocator *alloc,
+                                           void *stream, mc_tables **out, int64_t *node_offsets)
+{
+    if (out) *out = nullptr;
+    mc_graph *ug = nullptr;
+    mc_tables *t = nullptr;
+    mc_status st = guarded([&] {
+        MC_REQUIRE(out && node_offsets && graphs && colors && count >= 1, "bad batch arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<int64_t> noff(count + 1, 0), eoff(count + 1, 0);
+        for (int i = 0; i < count; ++i) {
+            MC_REQUIRE(graphs[i] && (colors[i] || graphs[i]->n == 0), "NULL graph or colours in batch");
+            noff[i + 1] = noff[i] + graphs[i]->n;
+            eoff[i + 1] = eoff[i] + graphs[i]->nnz;
+        }
+        const int64_t N = noff[count], NNZ = eoff[count];
+        MC_REQUIRE(N < (int64_t)0xffffffffLL, "batch has too many nodes");
+        Arena scratch;
+        if (alloc) { scratch.alloc.a = *alloc; scratch.alloc.custom = true; }
+        scratch.stream = s;
+        int64_t *urp = scratch.get<int64_t>((size_t)N + 1);
+        uint32_t *ucol = scratch.get<uint32_t>((size_t)(NNZ > 0 ? NNZ : 1));
+        uint8_t *ucolors = scratch.get<uint8_t>((size_t)(N > 0 ? N : 1));
+        for (int i = 0; i < count; ++i) {
+            const mc_graph *g = graphs[i];
+            if (g->n == 0) continue;
+            MC_LAUNCH("concat_csr", s, concat_csr_kernel<<<grid_for(std::max(g->n, g->nnz), 256), 256, 0, s>>>(
+                                           g->row_ptr, g->col, g->n, g->nnz, noff[i], eoff[i], urp, ucol));
+            MC_CUDA(cudaMemcpyAsync(ucolors + noff[i], colors[i], (size_t)g->n, cudaMemcpyDefault, s));
+        }
+        MC_CUDA(cudaMemcpyAsync(urp + N, &NNZ, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        mc_status s2 = mc_load_graph(N, NNZ, urp, ucol, MC_GRAPH_DEVICE_PTRS | MC_GRAPH_TRUSTED, alloc, stream, &ug);
+        if (s2 != MC_OK) throw Error(s2, std::string("batch graph: ") + mc_last_error());
+        s2 = mc_build_tables(ug, ucolors, k, count_bits, flags, alloc, stream, &t);
+        if (s2 != MC_OK) throw Error(s2, std::string("batch build: ") + mc_last_error());
+        t->owned_graph = ug;
+        ug = nullptr;
+        for (int i = 0; i <= count; ++i) node_offsets[i] = noff[i];
+    });
+    if (st != MC_OK) {
+        delete t;
+        mc_free_graph(ug);
+        return st;
+    }
+    *out = t;
+    return MC_OK;
 }
 
 extern "C" mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,

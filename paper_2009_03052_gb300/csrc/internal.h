@@ -133,6 +133,7 @@ struct mc_graph {
 
 struct mc_tables {
     const mc_graph *g = nullptr;
+    mc_graph *owned_graph = nullptr;  // the union graph of a batch build, freed with the tables
     int k = 0, bits = 64;
     bool zero_root = false;  // level k stored at colour-0 nodes only
     // copies per stored level-h entry sum: h, or 1 for a zero-rooted level k

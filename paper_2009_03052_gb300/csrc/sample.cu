@@ -305,7 +305,8 @@ struct SampleArgs {
     int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
     int k, h;
     const u128 *prefix;
-    u128 R;
+    u128 R;                     // total of the node range sampled from
+    u128 Xbase;                 // prefix before that range (0 for the whole graph)
     const uint32_t *bucket;     // root-search buckets (nb + 1 entries)
     u128 D;                     // bucket width
     uint64_t allow0, allow1;
@@ -529,6 +530,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
         V X = 0;
         uint32_t v = 0;
         if (ok && !draw_below(a.seed, index, 0, (V)a.R, X)) { ok = false; bad = true; }
+        X += (V)a.Xbase;  // a node range: the draw lands inside its part of the prefix
         if (ok) {
             const uint64_t bk = (uint64_t)(X / (V)a.D);
             int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
@@ -826,7 +828,9 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
 
 struct RootIndex {
     const u128 *prefix = nullptr;
-    u128 R = 0;
+    u128 R = 0;      // total of the node range
+    u128 base = 0;   // prefix before the range
+    u128 Rall = 0;   // total of all nodes
     const uint32_t *bucket = nullptr;
     u128 D = 1;
 };
@@ -835,8 +839,23 @@ void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allo
                        cudaStream_t s);
 void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t *start, cudaStream_t s);
 
+// Restrict a root index to the nodes [lo, hi) (hi <= 0: all nodes).
+static void restrict_range(RootIndex &ri, int64_t n, int64_t lo, int64_t hi, cudaStream_t s)
+{
+    ri.Rall = ri.R;
+    if (hi <= 0 && lo <= 0) return;
+    if (hi <= 0) hi = n;
+    MC_REQUIRE(lo >= 0 && lo < hi && hi <= n, "node range out of bounds");
+    u128 top = 0, base = 0;
+    MC_CUDA(cudaMemcpyAsync(&top, ri.prefix + (hi - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    if (lo > 0) MC_CUDA(cudaMemcpyAsync(&base, ri.prefix + (lo - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    ri.base = base;
+    ri.R = top - base;
+}
+
 static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scratch, int *err, cudaStream_t s,
-                            uint64_t &allow0, uint64_t &allow1)
+                            uint64_t &allow0, uint64_t &allow1, int64_t lo = 0, int64_t hi = 0)
 {
     const ShapeCatalog &cat = shape_catalog();
     allow0 = allow1 = 0;
@@ -851,6 +870,7 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
         ri.R = t->R[h];
         ri.bucket = t->bucket[h];
         ri.D = t->bucketD[h];
+        restrict_range(ri, t->g->n, lo, hi, s);
         return ri;
     }
     const int64_t n = t->g->n;
@@ -867,6 +887,7 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
     MC_CUDA(cudaStreamSynchronize(s));
     ri.prefix = p;
     ri.bucket = bk;
+    restrict_range(ri, n, lo, hi, s);
     return ri;
 }
 
@@ -879,7 +900,7 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     // 64-bit descent arithmetic is exact when 8 R < 2^64: every weight is at
     // most beta (<= 7) times a count of the level, every running sum at most
     // a level total
-    const bool narrow = t->bits == 64 && (a.R >> 61) == 0;
+    const bool narrow = t->bits == 64 && ((a.R + a.Xbase) >> 61) == 0;
     auto kern = t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t> : sample_kernel<uint64_t, u128>)
                               : sample_kernel<u128, u128>;
     int per_sm = 0;
@@ -981,9 +1002,10 @@ extern "C" mc_status mc_sigma(int h, int64_t *sigma_i, int64_t *sigma_ij)
     });
 }
 
-extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
-                               uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
-                               int32_t *shapes, int32_t *classes, void *stream)
+extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted_shape, int64_t node_lo,
+                                     int64_t node_hi, uint64_t seed, uint64_t first_index, int64_t count,
+                                     uint32_t *nodes, uint32_t *roots, int32_t *shapes, int32_t *classes,
+                                     void *stream)
 {
     return guarded([&] {
         MC_REQUIRE(t, "tables is NULL");
@@ -1000,10 +1022,11 @@ extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape
         MC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
         SampleArgs a;
         fill_sample_args(a, t, h);
-        RootIndex ri = root_index(t, h, unrooted_shape, scratch, err + 1, s, a.allow0, a.allow1);
+        RootIndex ri = root_index(t, h, unrooted_shape, scratch, err + 1, s, a.allow0, a.allow1, node_lo, node_hi);
         if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of the requested size/shape");
         a.prefix = ri.prefix;
         a.R = ri.R;
+        a.Xbase = ri.base;
         a.bucket = ri.bucket;
         a.D = ri.D;
         a.seed = seed;
@@ -1025,6 +1048,14 @@ extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape
         MC_CUDA(cudaStreamSynchronize(s));
         if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
     });
+}
+
+extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
+                               uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
+                               int32_t *shapes, int32_t *classes, void *stream)
+{
+    return mc_sample_range(t, h, unrooted_shape, 0, 0, seed, first_index, count, nodes, roots, shapes, classes,
+                           stream);
 }
 
 extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *p, double *est,
@@ -1056,10 +1087,11 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             MC_CUDA(cudaMemcpyAsync(dsig, cc->sigma_i.data(), (size_t)ncls * 8, cudaMemcpyHostToDevice, s));
             SampleArgs a;
             fill_sample_args(a, t, h);
-            RootIndex ri = root_index(t, h, -1, scratch, err + 1, s, a.allow0, a.allow1);
+            RootIndex ri = root_index(t, h, -1, scratch, err + 1, s, a.allow0, a.allow1, p->node_lo, p->node_hi);
             if (ri.R == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
             a.prefix = ri.prefix;
             a.R = ri.R;
+            a.Xbase = ri.base;
             a.bucket = ri.bucket;
             a.D = ri.D;
             a.seed = p->seed;
@@ -1100,7 +1132,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             std::vector<std::pair<uint64_t, uint64_t>> allows(nu);
             for (int j = 0; j < nu; ++j) {
                 uint64_t rooted[2], un[2];
-                mc_status s2 = mc_total(t, h, j, rooted, un, stream);
+                mc_status s2 = mc_total_range(t, h, j, p->node_lo, p->node_hi, rooted, un, stream);
                 if (s2 != MC_OK) throw Error(s2, "AGS: treelet totals failed");
                 tj[j] = (u128)un[0] | ((u128)un[1] << 64);
                 tjd[j] = (double)tj[j];
@@ -1128,7 +1160,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             };
             while (cur >= 0 && ncov < ncls && drawn < p->samples) {
                 if (!ris[cur].prefix) {
-                    ris[cur] = root_index(t, h, cur, scratch, err + 1, s, allows[cur].first, allows[cur].second);
+                    ris[cur] = root_index(t, h, cur, scratch, err + 1, s, allows[cur].first, allows[cur].second,
+                                          p->node_lo, p->node_hi);
                 }
                 const int64_t b = std::min(B, p->samples - drawn);
                 SampleArgs a;
@@ -1137,6 +1170,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.allow1 = allows[cur].second;
                 a.prefix = ris[cur].prefix;
                 a.R = ris[cur].R;
+                a.Xbase = ris[cur].base;
                 a.bucket = ris[cur].bucket;
                 a.D = ris[cur].D;
                 a.seed = p->seed;
