@@ -234,6 +234,51 @@ mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint64_t seed, 
                                       int64_t samples, double *est, uint64_t *hits, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of requests over device-resident tables      */
+/* ------------------------------------------------------------------------ */
+/* A server keeps built tables on the device and runs sample and estimate
+ * requests on a pool of `slots` workers, each with its own CUDA stream.
+ * Requests queue in arrival order; the first queued request starts as soon
+ * as a worker is idle and its device buffers fit `memory_budget` bytes (0:
+ * half of the free device memory at creation; a request larger than the
+ * budget runs alone).  Requests that arrive while others run are admitted as
+ * workers and memory free up, and their work overlaps on the device.  A
+ * request's result depends only on the tables, its seed and its sample
+ * indices: it is the same alone and in any mix.  The tables must outlive the
+ * server; tables built without an allocator use stream-ordered memory for
+ * their per-call scratch, so workers never synchronise the device to
+ * allocate. */
+typedef struct mc_server mc_server;
+
+#define MC_REQ_SAMPLE 0
+#define MC_REQ_ESTIMATE 1
+
+typedef struct {
+    int kind;                  /* MC_REQ_SAMPLE or MC_REQ_ESTIMATE */
+    int table;                 /* index into the server's tables */
+    int h;                     /* sample requests: treelet size */
+    int32_t unrooted_shape;    /* sample requests: -1 for all shapes */
+    int64_t node_lo, node_hi;  /* sample requests: root range (node_hi <= 0: all nodes) */
+    uint64_t seed, first_index;
+    int64_t count;             /* sample requests: number of samples */
+    mc_estimate_params est;    /* estimate requests */
+} mc_request;
+
+mc_status mc_server_create(const mc_tables *const *tables, int n_tables, int slots, size_t memory_budget,
+                           mc_server **out);
+/* Queue a request (returns at once); *id identifies it. */
+mc_status mc_server_submit(mc_server *server, const mc_request *request, int64_t *id);
+/* Wait for request `id` and copy its results to host buffers (any may be
+ * NULL): sample requests fill nodes[count*h] (each sample's nodes ascending)
+ * and classes[count]; estimate requests fill est[N_h] and hits[N_h].
+ * queue_us: submit to start; latency_us: submit to completion.  A request's
+ * results are delivered once. */
+mc_status mc_server_wait(mc_server *server, int64_t id, uint32_t *nodes, int32_t *classes, double *est,
+                         uint64_t *hits, double *queue_us, double *latency_us);
+/* Stop the workers after their current requests and free the server. */
+void mc_server_free(mc_server *server);
+
+/* ------------------------------------------------------------------------ */
 /* Catalogue (computed on the current device on first use, then cached)      */
 /* ------------------------------------------------------------------------ */
 int mc_num_shapes(int h);          /* rooted treelet shapes on h nodes */

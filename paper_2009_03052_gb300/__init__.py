@@ -25,6 +25,8 @@ MC_OK, MC_E_INVALID, MC_E_NOMEM, MC_E_OVERFLOW, MC_E_CUDA, MC_E_TIMEOUT, MC_E_UN
 MC_GRAPH_DEVICE_PTRS = 1
 MC_GRAPH_TRUSTED = 2
 MC_BUILD_ZERO_ROOT = 1
+MC_REQ_SAMPLE = 0
+MC_REQ_ESTIMATE = 1
 MC_EST_UNIFORM = 0
 MC_EST_AGS = 1
 
@@ -34,7 +36,8 @@ EXPORTED = [
     "mc_estimate_counts", "mc_num_shapes", "mc_num_unrooted", "mc_num_classes", "mc_shape_info",
     "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
     "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
-    "mc_sample_range", "mc_build_tables_batch",
+    "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
+    "mc_server_wait", "mc_server_free",
 ]
 
 
@@ -59,6 +62,12 @@ class EstimateParams(C.Structure):
                 ("first_index", C.c_uint64), ("samples", C.c_int64), ("cbar", C.c_int64),
                 ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64),
                 ("node_lo", C.c_int64), ("node_hi", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("table", C.c_int), ("h", C.c_int), ("unrooted_shape", C.c_int32),
+                ("node_lo", C.c_int64), ("node_hi", C.c_int64), ("seed", C.c_uint64),
+                ("first_index", C.c_uint64), ("count", C.c_int64), ("est", EstimateParams)]
 
 
 class EstimateStats(C.Structure):
@@ -106,6 +115,12 @@ def load(path: str | None = None):
         lib.mc_profile_read.argtypes = [P, C.c_size_t, P, P, P, C.c_int, C.POINTER(C.c_int)]
         lib.mc_launch_count.restype = C.c_int64
         lib.mc_estimate_uniform_noalloc.argtypes = [P, C.c_int, u64, u64, i64, P, P, P]
+        lib.mc_server_create.argtypes = [P, C.c_int, C.c_int, C.c_size_t, C.POINTER(P)]
+        lib.mc_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(i64)]
+        lib.mc_server_wait.argtypes = [P, i64, P, P, P, P, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
+        lib.mc_server_free.argtypes = [P]
+        lib.mc_server_free.restype = None
         _lib = lib
         return lib
 
@@ -240,7 +255,7 @@ class Tables:
     """mc_build_tables: the exact colourful treelet count tables."""
 
     def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None,
-                 zero_root: bool = False, _handle=None):
+                 zero_root: bool = False, own_memory: bool = False, _handle=None):
         torch = _torch()
         if _handle is not None:  # built by batch()
             self.graph, self.k, self.bits, self._alloc, self.handle = graph, k, count_bits, \
@@ -251,9 +266,11 @@ class Tables:
         self.graph, self.k, self.bits = graph, k, count_bits
         self._alloc = torch_allocator()
         h = C.c_void_p()
+        # own_memory: the library allocates (stream-ordered scratch, no
+        # callbacks into Python), e.g. for tables served from worker threads
         _check(load().mc_build_tables(graph.handle, _ptr(colors) if graph.n else None, k,
                                       count_bits, MC_BUILD_ZERO_ROOT if zero_root else 0,
-                                      C.byref(self._alloc.struct),
+                                      None if own_memory else C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
 
@@ -434,3 +451,69 @@ def profile_read(with_bytes: bool = False) -> dict:
 
 def launch_count() -> int:
     return int(load().mc_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+class Server:
+    """mc_server_*: continuous batching of sample / estimate requests over
+    device-resident tables (which must outlive the server)."""
+
+    def __init__(self, tables: list, slots: int = 4, memory_budget: int = 0):
+        self.tables = list(tables)
+        arr = (C.c_void_p * len(tables))(*[t.handle.value for t in tables])
+        h = C.c_void_p()
+        _check(load().mc_server_create(arr, len(tables), slots, memory_budget, C.byref(h)))
+        self.handle = h
+        self._req = {}
+
+    def submit_sample(self, table: int, h: int, seed: int, count: int, first_index: int = 0,
+                      unrooted: int = -1, node_range=(0, 0)) -> int:
+        r = Request(MC_REQ_SAMPLE, table, h, unrooted, node_range[0], node_range[1], seed,
+                    first_index, count, EstimateParams())
+        i = C.c_int64()
+        _check(load().mc_server_submit(self.handle, C.byref(r), C.byref(i)))
+        self._req[i.value] = ("sample", h, count)
+        return i.value
+
+    def submit_estimate(self, table: int, h: int, seed: int, samples: int,
+                        mode: int = MC_EST_UNIFORM, first_index: int = 0, cbar: int = 0,
+                        eps: float = 0.0, delta: float = 0.0, batch: int = 0,
+                        node_range=(0, 0)) -> int:
+        e = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
+                           node_range[0], node_range[1])
+        r = Request(MC_REQ_ESTIMATE, table, 0, -1, 0, 0, 0, 0, 0, e)
+        i = C.c_int64()
+        _check(load().mc_server_submit(self.handle, C.byref(r), C.byref(i)))
+        self._req[i.value] = ("estimate", h, 0)
+        return i.value
+
+    def wait(self, rid: int) -> dict:
+        kind, h, count = self._req.pop(rid)
+        q, lat = C.c_double(), C.c_double()
+        if kind == "sample":
+            nodes = np.zeros(max(count * h, 1), np.uint32)
+            cls = np.zeros(max(count, 1), np.int32)
+            _check(load().mc_server_wait(self.handle, rid, _ptr(nodes), _ptr(cls), None, None,
+                                         C.byref(q), C.byref(lat)))
+            return {"nodes": nodes[: count * h].reshape(count, h), "classes": cls[:count],
+                    "queue_us": q.value, "latency_us": lat.value}
+        nc = num_classes(h)
+        est = np.zeros(nc, np.float64)
+        hits = np.zeros(nc, np.uint64)
+        _check(load().mc_server_wait(self.handle, rid, None, None, _ptr(est), _ptr(hits),
+                                     C.byref(q), C.byref(lat)))
+        return {"est": est, "hits": hits, "queue_us": q.value, "latency_us": lat.value}
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().mc_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

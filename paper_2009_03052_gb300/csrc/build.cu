@@ -751,7 +751,7 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         t->geo = make_geometry(k);
         t->arena.stream = s;
         if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
-        Arena scratch;
+        Arena scratch(true);
         scratch.alloc = t->arena.alloc;
         scratch.stream = s;
         const int64_t n = g->n;
@@ -828,7 +828,7 @@ void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
     std::lock_guard<std::mutex> lock(t->idx_mu);
     if (t->prefix[h] || h < 2) return;
     const int64_t n = t->g->n;
-    Arena scratch;
+    Arena scratch(true);
     scratch.alloc = t->arena.alloc;
     scratch.stream = s;
     int *err = scratch.get<int>(1);
@@ -883,7 +883,7 @@ extern "C" mc_status mc_total_range(const mc_tables *t, int h, int32_t unrooted_
             // the level's node prefix (all shapes: the cached root index; one
             // unrooted shape: computed here), read at the range's ends
             const u128 *pre = nullptr;
-            Arena scratch;
+            Arena scratch(true);
             scratch.alloc = t->arena.alloc;
             scratch.stream = s;
             int *err = scratch.get<int>(1);
@@ -960,7 +960,7 @@ extern "C" mc_status mc_build_tables_batch(int count, const mc_graph *const *gra
         }
         const int64_t N = noff[count], NNZ = eoff[count];
         MC_REQUIRE(N < (int64_t)0xffffffffLL, "batch has too many nodes");
-        Arena scratch;
+        Arena scratch(true);
         if (alloc) { scratch.alloc.a = *alloc; scratch.alloc.custom = true; }
         scratch.stream = s;
         int64_t *urp = scratch.get<int64_t>((size_t)N + 1);

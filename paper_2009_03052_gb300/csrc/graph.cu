@@ -35,7 +35,10 @@ void Allocator::release(void *p, size_t bytes, cudaStream_t s) const
 
 void Arena::release_all()
 {
-    for (auto &b : blocks) alloc.release(b.first, b.second, stream);
+    for (auto &b : blocks) {
+        if (scratch && !alloc.custom) cudaFreeAsync(b.first, stream);
+        else alloc.release(b.first, b.second, stream);
+    }
     blocks.clear();
 }
 
@@ -327,7 +330,7 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
         const bool on_dev = flags & MC_GRAPH_DEVICE_PTRS;
         const bool trusted = flags & MC_GRAPH_TRUSTED;
         const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        Arena scratch;
+        Arena scratch(true);
         scratch.alloc = g->arena.alloc;
         scratch.stream = s;
         int64_t *dstat = scratch.get<int64_t>(4);  // flags, max degree, #chunks, #hubs

@@ -45,16 +45,27 @@ struct Allocator {
     void release(void *p, size_t bytes, cudaStream_t s) const;
 };
 
-// A set of device buffers released together.
+// A set of device buffers released together.  A scratch arena (buffers of
+// one call, used on its stream only) takes stream-ordered memory
+// (cudaMallocAsync) when no allocator is given, so concurrent calls on
+// different streams never synchronise the device to allocate.
 struct Arena {
     Allocator alloc;
     cudaStream_t stream = nullptr;
+    bool scratch = false;
     std::vector<std::pair<void *, size_t>> blocks;
+    Arena() = default;
+    explicit Arena(bool is_scratch) : scratch(is_scratch) {}
     template <typename T> T *get(size_t count)
     {
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 256;
-        void *p = alloc.alloc(bytes, stream);
+        void *p = nullptr;
+        if (scratch && !alloc.custom) {
+            if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) { cudaGetLastError(); p = nullptr; }
+        } else {
+            p = alloc.alloc(bytes, stream);
+        }
         if (!p) throw Error(MC_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
         blocks.emplace_back(p, bytes);
         return static_cast<T *>(p);

@@ -1015,7 +1015,7 @@ extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted
         if (count == 0) return;
         cudaStream_t s = (cudaStream_t)stream;
         const ClassCatalog *cc = class_catalog(h);
-        Arena scratch;
+        Arena scratch(true);
         scratch.alloc = t->arena.alloc;
         scratch.stream = s;
         int *err = scratch.get<int>(2);
@@ -1071,7 +1071,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         const ClassCatalog *cc = class_catalog_sigma(h);
         const int ncls = (int)cc->codes.size();
         const ShapeCatalog &cat = shape_catalog();
-        Arena scratch;
+        Arena scratch(true);
         scratch.alloc = t->arena.alloc;
         scratch.stream = s;
         int *err = scratch.get<int>(2);

@@ -1,0 +1,226 @@
+// serve.cu -- a request loop over device-resident tables: continuous
+// batching of sample and estimate requests on a pool of slots.
+//
+// Every slot is a host thread with its own CUDA stream.  Requests queue in
+// arrival order; the first queued request is admitted as soon as a slot is
+// idle and its device buffers fit the memory budget, so requests that
+// arrive while others run start at once on another slot and their kernels
+// overlap on the device.  A request's results depend only on the tables,
+// its seed and its sample indices, so they are the same alone or in a mix.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+
+#include "internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    mc_request r{};
+    size_t mem = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    mc_status status = MC_OK;
+    std::string error;
+    std::vector<uint32_t> nodes;
+    std::vector<int32_t> classes;
+    std::vector<double> est;
+    std::vector<uint64_t> hits;
+    Clock::time_point t_submit, t_start, t_done;
+};
+
+}  // namespace
+
+struct mc_server {
+    std::vector<const mc_tables *> tables;
+    size_t budget = 0, in_use = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<int64_t> queue;
+    std::map<int64_t, Request> reqs;
+    int64_t next_id = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+};
+
+namespace mc {
+
+// device bytes a request needs while it runs
+static size_t request_memory(const mc_request &r)
+{
+    if (r.kind == MC_REQ_SAMPLE) return (size_t)r.count * ((size_t)r.h + 1) * 4 + (1 << 20);
+    return (size_t)4 << 20;  // estimates: histogram, class ids of one AGS batch, scratch
+}
+
+static void run_request(mc_server *sv, Request &q, cudaStream_t s)
+{
+    const mc_tables *t = sv->tables[q.r.table];
+    if (q.r.kind == MC_REQ_SAMPLE) {
+        uint32_t *dn = nullptr;
+        int32_t *dc = nullptr;
+        const int64_t n = q.r.count;
+        MC_CUDA(cudaMallocAsync(&dn, (size_t)std::max<int64_t>(n, 1) * q.r.h * 4, s));
+        MC_CUDA(cudaMallocAsync(&dc, (size_t)std::max<int64_t>(n, 1) * 4, s));
+        mc_status st = mc_sample_range(t, q.r.h, q.r.unrooted_shape, q.r.node_lo, q.r.node_hi, q.r.seed,
+                                       q.r.first_index, n, dn, nullptr, nullptr, dc, (void *)s);
+        if (st == MC_OK) {
+            q.nodes.resize((size_t)n * q.r.h);
+            q.classes.resize((size_t)n);
+            if (n) {
+                MC_CUDA(cudaMemcpyAsync(q.nodes.data(), dn, q.nodes.size() * 4, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaMemcpyAsync(q.classes.data(), dc, q.classes.size() * 4, cudaMemcpyDeviceToHost, s));
+            }
+        }
+        cudaFreeAsync(dn, s);
+        cudaFreeAsync(dc, s);
+        MC_CUDA(cudaStreamSynchronize(s));
+        if (st != MC_OK) throw Error(st, mc_last_error());
+    } else {
+        const int nc = mc_num_classes(q.r.est.h);
+        if (nc < 0) throw Error(MC_E_INVALID, mc_last_error());
+        q.est.assign((size_t)nc, 0.0);
+        q.hits.assign((size_t)nc, 0);
+        mc_status st = mc_estimate_counts(t, &q.r.est, q.est.data(), q.hits.data(), nullptr, (void *)s);
+        if (st != MC_OK) throw Error(st, mc_last_error());
+    }
+}
+
+static void worker(mc_server *sv)
+{
+    cudaSetDevice(sv->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        int64_t id = 0;
+        {
+            std::unique_lock<std::mutex> lock(sv->mu);
+            sv->cv.wait(lock, [&] {
+                if (sv->stop) return true;
+                if (sv->queue.empty()) return false;
+                const Request &head = sv->reqs.at(sv->queue.front());
+                return sv->in_use + head.mem <= sv->budget || sv->in_use == 0;
+            });
+            if (sv->stop) break;
+            id = sv->queue.front();
+            sv->queue.pop_front();
+            Request &q = sv->reqs.at(id);
+            sv->in_use += q.mem;
+            q.state = 1;
+            q.t_start = Clock::now();
+        }
+        Request *qp;
+        {
+            std::lock_guard<std::mutex> lock(sv->mu);
+            qp = &sv->reqs.at(id);
+        }
+        mc_status st = guarded([&] { run_request(sv, *qp, s); });
+        {
+            std::lock_guard<std::mutex> lock(sv->mu);
+            qp->status = st;
+            if (st != MC_OK) qp->error = mc_last_error();
+            qp->state = 2;
+            qp->t_done = Clock::now();
+            sv->in_use -= qp->mem;
+        }
+        sv->cv.notify_all();
+    }
+    cudaStreamDestroy(s);
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+extern "C" mc_status mc_server_create(const mc_tables *const *tables, int n_tables, int slots, size_t memory_budget,
+                                      mc_server **out)
+{
+    if (out) *out = nullptr;
+    mc_server *sv = nullptr;
+    mc_status st = guarded([&] {
+        MC_REQUIRE(out && tables && n_tables >= 1 && slots >= 1 && slots <= 64, "bad server arguments");
+        sv = new mc_server();
+        for (int i = 0; i < n_tables; ++i) {
+            MC_REQUIRE(tables[i], "NULL tables");
+            sv->tables.push_back(tables[i]);
+        }
+        MC_CUDA(cudaGetDevice(&sv->device));
+        if (memory_budget == 0) {
+            size_t free_b = 0, total_b = 0;
+            MC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            memory_budget = free_b / 2;
+        }
+        sv->budget = memory_budget;
+        for (int i = 0; i < slots; ++i) sv->workers.emplace_back(worker, sv);
+    });
+    if (st != MC_OK) { delete sv; return st; }
+    *out = sv;
+    return MC_OK;
+}
+
+extern "C" mc_status mc_server_submit(mc_server *sv, const mc_request *r, int64_t *id)
+{
+    return guarded([&] {
+        MC_REQUIRE(sv && r && id, "NULL argument");
+        MC_REQUIRE(r->table >= 0 && r->table < (int)sv->tables.size(), "table index out of range");
+        const mc_tables *t = sv->tables[r->table];
+        if (r->kind == MC_REQ_SAMPLE) {
+            MC_REQUIRE(r->h >= 2 && r->h <= t->k && r->count >= 0, "bad sample request");
+        } else {
+            MC_REQUIRE(r->kind == MC_REQ_ESTIMATE, "unknown request kind");
+            MC_REQUIRE(r->est.h >= 2 && r->est.h <= t->k, "bad estimate request");
+        }
+        std::lock_guard<std::mutex> lock(sv->mu);
+        const int64_t i = sv->next_id++;
+        Request &q = sv->reqs[i];
+        q.r = *r;
+        q.mem = request_memory(*r);
+        q.t_submit = Clock::now();
+        sv->queue.push_back(i);
+        *id = i;
+        sv->cv.notify_all();
+    });
+}
+
+extern "C" mc_status mc_server_wait(mc_server *sv, int64_t id, uint32_t *nodes, int32_t *classes, double *est,
+                                    uint64_t *hits, double *queue_us, double *latency_us)
+{
+    Request q;
+    mc_status st = guarded([&] {
+        MC_REQUIRE(sv, "server is NULL");
+        std::unique_lock<std::mutex> lock(sv->mu);
+        auto it = sv->reqs.find(id);
+        MC_REQUIRE(it != sv->reqs.end(), "unknown request id");
+        sv->cv.wait(lock, [&] { return sv->reqs.at(id).state == 2; });
+        q = std::move(sv->reqs.at(id));
+        sv->reqs.erase(id);
+    });
+    if (st != MC_OK) return st;
+    if (q.status != MC_OK) {
+        set_last_error(q.error);
+        return q.status;
+    }
+    if (nodes && !q.nodes.empty()) std::copy(q.nodes.begin(), q.nodes.end(), nodes);
+    if (classes && !q.classes.empty()) std::copy(q.classes.begin(), q.classes.end(), classes);
+    if (est && !q.est.empty()) std::copy(q.est.begin(), q.est.end(), est);
+    if (hits && !q.hits.empty()) std::copy(q.hits.begin(), q.hits.end(), hits);
+    using us = std::chrono::duration<double, std::micro>;
+    if (queue_us) *queue_us = us(q.t_start - q.t_submit).count();
+    if (latency_us) *latency_us = us(q.t_done - q.t_submit).count();
+    return MC_OK;
+}
+
+extern "C" void mc_server_free(mc_server *sv)
+{
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    for (auto &w : sv->workers) w.join();
+    delete sv;
+}
