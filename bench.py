@@ -443,6 +443,53 @@ def run_batch(args):
 
 
 # ---------------------------------------------------------------------------
+# R-MAT scale 22, k = 7: build plus 10M adaptive samples
+# ---------------------------------------------------------------------------
+def run_rmat(args):
+    import torch
+    import paper_2009_03052_gb300 as M
+    M.build()
+    M.load()
+    k, bits, samples = 7, 128, 10_000_000
+    g = synth.rmat(22, 16, seed=0)
+    G = M.Graph.from_csr(g, trusted=True)
+    colbuf = torch.empty(g.n, dtype=torch.uint8, device="cuda")
+    M.sigma(k)
+    s = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i & 0xFF)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(s)
+        col = M.color(G, k, 500 + i, out=colbuf)
+        T = M.Tables(G, col, k, bits)
+        T.total(k)
+        e[1].record(s)
+        t0 = time.perf_counter()
+        est, hits, st = T.estimate(k, seed=i, samples=samples, mode=M.MC_EST_AGS, cbar=1000)
+        e[2].record(s)
+        e[2].synchronize()
+        T.free()
+        if i >= args.warmup:
+            res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), st))
+    build_ms = statistics.median(r[0] for r in res)
+    ags_ms = statistics.median(r[1] for r in res)
+    entries = g.n * live_entries_per_node(k)
+    st = res[-1][2]
+    print(json.dumps({
+        "metric": "DP table entries/s", "value": entries / (build_ms / 1e3), "unit": "entries/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": build_ms + ags_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128",
+        "data": "synthetic",
+        "config": {"workload": "rmat22_k7_ags10m", "n": g.n, "m": g.m, "k": k, "count_bits": bits,
+                   "rmat": [0.57, 0.19, 0.19], "edge_factor": 16, "ags_samples": samples,
+                   "cbar": 1000, "l2": "flushed between steps"},
+        "build_ms": build_ms, "ags_ms": ags_ms,
+        "ags_samples_per_s": st["samples"] / (ags_ms / 1e3), "ags_stats": st}), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # serving: a Poisson stream of requests over device-resident k = 8 tables
 # ---------------------------------------------------------------------------
 def run_serve(args):
@@ -528,9 +575,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--small", action="store_true", help="the 1k-node ER case (k = 4)")
-    ap.add_argument("--workload", choices=["default", "batch", "serve"], default="default",
+    ap.add_argument("--workload", choices=["default", "batch", "serve", "rmat"], default="default",
                     help="batch: 96 instances built in one pass vs one by one (k = 6, u128); "
-                         "serve: a request stream over k = 8 tables")
+                         "serve: a request stream over k = 8 tables; "
+                         "rmat: R-MAT scale 22, k = 7, build + 10M adaptive samples")
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
@@ -547,6 +595,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "rmat":
+        run_rmat(args)
     else:
         run_gpu(args, rank, world, local_rank)
 

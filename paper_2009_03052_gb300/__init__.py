@@ -363,6 +363,7 @@ class Tables:
         return est, hits, {"samples": st.samples, "switches": st.switches,
                            "covered": st.covered, "batches": st.batches,
                            "discarded": st.discarded}
+
     def estimate_noalloc(self, h: int, seed: int, samples: int, first_index: int = 0,
                          stream=None):
         """mc_estimate_uniform_noalloc: the uniform estimate without any

@@ -8,6 +8,8 @@ from __future__ import annotations
 import itertools
 from collections import Counter
 
+import numpy as np
+
 from oracle import catalog as cat
 
 
@@ -136,4 +138,26 @@ def graphlets(g, h, classify) -> Counter:
     for S in itertools.combinations(range(g.n), h):
         if is_connected(adj, S):
             out[classify(word_of(adj, S))] += 1
+    return out
+
+
+def colour_counts(g, colors, k):
+    """[n, k] neighbour counts per colour."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), g.degrees())
+    idx = src * k + colors[g.col.astype(np.int64)].astype(np.int64)
+    return np.bincount(idx, minlength=g.n * k).reshape(g.n, k)
+
+
+def star_totals(g, colors, k):
+    """{h: number of colourful h-stars}, h = 2..k, as exact integers."""
+    cnt = colour_counts(g, colors, k)
+    cnt[np.arange(g.n), colors.astype(np.int64)] = 0      # neighbours of the centre's colour
+    e = [np.ones(g.n, dtype=object)] + [np.zeros(g.n, dtype=object) for _ in range(k - 1)]
+    for a in range(k):
+        x = cnt[:, a].astype(object)
+        for j in range(k - 1, 0, -1):
+            e[j] = e[j] + e[j - 1] * x
+    out = {2: int(e[1].sum()) // 2}
+    for h in range(3, k + 1):
+        out[h] = int(e[h - 1].sum())
     return out

@@ -193,3 +193,17 @@ def test_zero_rooting_keeps_each_copy_once(oracle, k):
         assert np.array_equal(la[zero], lz[zero]) and not lz[~zero].any()
         for h in range(1, k):
             assert np.array_equal(A.level(h), Z.level(h))
+
+
+def test_star_totals_closed_form_any_graph(oracle):
+    # For h >= 3 an h-star has one centre; its colourful copies centred at v
+    # choose h-1 neighbours of distinct colours, none c_v: the star total is
+    # sum_v e_{h-1}(per-colour neighbour counts of v without c_v).
+    k = 6
+    g = synth.rmat(9, 12, seed=3)
+    colors = synth.random_colors(g.n, k, seed=5)
+    T = oracle.Tables(g, colors, k, 128)
+    stars = brute.star_totals(g, colors, k)
+    assert T.total(2)[1] == stars[2]
+    for h in range(3, k + 1):
+        assert T.total(h, cat.unrooted_id("10" * (h - 1)))[1] == stars[h]
