@@ -74,8 +74,8 @@ def _load():
         lib.oc_draw_below.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, u64p, u64p]
         lib.oc_build.restype = P
         lib.oc_build.argtypes = [C.c_int64, i64p, u32p, u8p, C.c_int, C.c_int, C.c_int,
-                                 i32p, i32p, i32p, i32p, i32p, i32p, C.c_int, C.c_int,
-                                 C.POINTER(C.c_int)]
+                                 i32p, i32p, i32p, i32p, i32p, i32p, i32p, C.c_int, C.c_int,
+                                 C.c_int, C.POINTER(C.c_int)]
         lib.oc_free.argtypes = [P]
         lib.oc_read_level.argtypes = [P, C.c_int, u64p]
         lib.oc_neighbor_sum.argtypes = [P, C.c_int, C.c_int64, u64p]
@@ -90,11 +90,14 @@ def _load():
         lib.oc_spanning_trees.restype = C.c_int64
         lib.oc_spanning_trees.argtypes = [C.c_int, C.c_uint32]
         lib.oc_sigma_matrix.argtypes = [C.c_int, C.c_int, i32p, i32p, i32p, i32p, i32p, i32p,
-                                        C.c_int, i64p, C.c_int]
+                                        i32p, C.c_int, i64p, C.c_int]
         lib.oc_estimate_uniform.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64,
-                                            i64p, f64p, u64p]
+                                            i64p, C.c_int64, i64p, f64p, u64p]
         lib.oc_estimate_ags.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
-                                        i64p, C.c_int, f64p, u64p, i64p]
+                                        i64p, C.c_int, C.c_int64, i64p, i64p, f64p, u64p, i64p]
+        lib.oc_star_total.argtypes = [P, C.c_int, u64p]
+        lib.oc_sample_stars.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64,
+                                        u32p, u32p, i32p]
         _lib = lib
         return lib
 
@@ -141,8 +144,9 @@ def color(n: int, k: int, seed: int) -> np.ndarray:
 
 def _catalog_arrays(cat: "_cat.Catalog"):
     a = lambda x: np.ascontiguousarray(np.asarray(x, np.int32))
+    copies = [c for h in range(1, cat.k + 1) for c in cat.copies_divisor(h)]
     return (len(cat.strings), a(cat.size), a(cat.local), a(cat.left), a(cat.right),
-            a(cat.beta), a(cat.unrooted))
+            a(cat.beta), a(cat.unrooted), a(copies))
 
 
 def num_classes(h: int) -> int:
@@ -202,11 +206,11 @@ class Tables:
     """Exact count tables c(T_C, v) for |T| = 1..k (Section 2.1, Eq. 1)."""
 
     def __init__(self, graph, colors, k: int, width: int = 128, nthreads: int | None = None,
-                 zero_root: bool = False):
+                 zero_root: bool = False, skip_round: bool = False):
         lib = _load()
-        self.k, self.width, self.zero_root = k, width, zero_root
+        self.k, self.width, self.zero_root, self.skip_round = k, width, zero_root, skip_round
         self.n = int(graph.n)
-        self.cat = _cat.Catalog(k)
+        self.cat = _cat.Catalog(k, skip_round)
         nsh, *arrs = _catalog_arrays(self.cat)
         self._keep = arrs
         colors = np.ascontiguousarray(np.asarray(colors, np.uint8))
@@ -218,7 +222,7 @@ class Tables:
         h = lib.oc_build(self.n, np.ascontiguousarray(graph.row_ptr, np.int64),
                          np.ascontiguousarray(graph.col, np.uint32), colors if self.n else
                          np.zeros(1, np.uint8), k, width, nsh, *arrs, nthreads,
-                         1 if zero_root else 0, C.byref(st))
+                         1 if zero_root else 0, 1 if skip_round else 0, C.byref(st))
         _check(st.value, "build")
         self._h = h
 
@@ -248,8 +252,23 @@ class Tables:
         _check(_load().oc_neighbor_sum(self._h, h, v, out))
         return out.reshape(r, q, 2)
 
+    def star_total(self, h: int) -> int:
+        """S = sum_v C(d_v, h-1): the h-stars of the graph."""
+        out = np.zeros(2, np.uint64)
+        _check(_load().oc_star_total(self._h, h, out))
+        return _u128(out)
+
+    def sample_stars(self, h: int, seed: int, first_index: int, count: int):
+        """Uncoloured h-stars: (nodes [count, h] ascending, centres, class ids)."""
+        nodes = np.zeros(max(count * h, 1), np.uint32)
+        centres = np.zeros(max(count, 1), np.uint32)
+        classes = np.zeros(max(count, 1), np.int32)
+        _check(_load().oc_sample_stars(self._h, h, seed, first_index, count, nodes, centres,
+                                       classes), "stars")
+        return nodes[: count * h].reshape(count, h), centres[:count], classes[:count]
+
     def total(self, h: int, unrooted: int = -1) -> tuple[int, int]:
-        """(rooted total R, unrooted count R / h)."""
+        """(rooted total R, unrooted count: R_j / h per shape j, summed)."""
         R = np.zeros(2, np.uint64)
         U = np.zeros(2, np.uint64)
         _check(_load().oc_total(self._h, h, unrooted, R, U))
@@ -266,23 +285,35 @@ class Tables:
         return (nodes[: count * h].reshape(count, h), roots[:count], shapes[:count],
                 classes[:count])
 
-    def estimate_uniform(self, h: int, seed: int, n_samples: int, first_index: int = 0):
-        s_i, _ = sigma(h)
-        est = np.zeros(len(s_i), np.float64)
-        hits = np.zeros(len(s_i), np.uint64)
+    def _skip_sigmas(self, h: int):
+        """(sigma'_i = sum_j sigma_ij a_j, sigma*_i = spanning stars of H_i) for a
+        round-skipped level k; (sigma_i, zeros) otherwise."""
+        s_i, s_ij = sigma(h)
+        if not (self.skip_round and h == self.k):
+            return s_i, np.zeros_like(s_i)
+        a = np.asarray(self.cat.copies_divisor(h), np.int64)
+        star = _cat.unrooted_id("10" * (h - 1))
+        return (np.ascontiguousarray(s_ij @ a), np.ascontiguousarray(s_ij[:, star]))
+
+    def estimate_uniform(self, h: int, seed: int, n_samples: int, first_index: int = 0,
+                         star_samples: int = 0):
+        s_use, s_star = self._skip_sigmas(h)
+        est = np.zeros(len(s_use), np.float64)
+        hits = np.zeros(len(s_use), np.uint64)
         _check(_load().oc_estimate_uniform(self._h, h, seed, first_index, n_samples,
-                                           np.ascontiguousarray(s_i), est, hits))
+                                           s_use, star_samples, s_star, est, hits))
         return est, hits
 
     def estimate_ags(self, h: int, seed: int, max_samples: int, cbar: int = 1000,
-                     first_index: int = 0):
+                     first_index: int = 0, star_samples: int = 0):
         _, s_ij = sigma(h)
+        s_prime, s_star = self._skip_sigmas(h)
         est = np.zeros(s_ij.shape[0], np.float64)
         hits = np.zeros(s_ij.shape[0], np.uint64)
         stats = np.zeros(3, np.int64)
         _check(_load().oc_estimate_ags(self._h, h, seed, first_index, max_samples, cbar,
-                                       np.ascontiguousarray(s_ij), s_ij.shape[1], est, hits,
-                                       stats))
+                                       np.ascontiguousarray(s_ij), s_ij.shape[1], star_samples,
+                                       s_prime, s_star, est, hits, stats))
         return est, hits, {"samples": int(stats[0]), "switches": int(stats[1]),
                            "covered": int(stats[2])}
 

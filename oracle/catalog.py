@@ -18,6 +18,10 @@ unrooted shape of each rooting.
   beta_T is the number of root children whose subtree equals T''.
 * Unrooted shapes: the code of an unrooted tree is the smallest s_T over all
   of its rootings; unrooted ids within a size ascend with that code.
+* Round skipping (Section 3.3.2): level k uses a balanced decomposition in
+  which both parts have at most k-2 nodes, so level k-1 is never needed;
+  rooted k-shapes without one (every star rooting, every leaf rooting) are
+  not counted.
 
 Trees are handled as strings over {0,1} throughout; this is slow and plain
 on purpose.
@@ -97,6 +101,30 @@ def decompose(s: str) -> tuple[str, str, int]:
     return "".join(kids[1:]), first[1:-1], beta
 
 
+def balanced_decompose(s: str, k: int):
+    """Balanced decomposition used when round k-1 is skipped (Section 3.3.2):
+    T'' is the subtree of the first root child, in the order the children
+    appear in s_T, whose size is between 2 and k-2; T' is T without that
+    subtree, and beta_T counts the root children whose subtree equals T''.
+    Returns (s_T', s_T'', beta_T), or None when no root child qualifies --
+    such rooted shapes are not counted at level k."""
+    kids = _split_children(s)
+    for c in kids:
+        if 2 <= len(c) // 2 <= k - 2:
+            rest = list(kids)
+            rest.remove(c)
+            return "".join(rest), c[1:-1], kids.count(c)
+    return None
+
+
+def balanced_rootings(code: int, h: int) -> int:
+    """a_j: the number of nodes x of the unrooted h-tree with this code such
+    that the tree rooted at x has a balanced decomposition (h = k)."""
+    s = format(code, "0%db" % (2 * (h - 1))) if h > 1 else ""
+    adj = decode(s)
+    return sum(1 for x in adj if balanced_decompose(encode(adj, x), h) is not None)
+
+
 def unrooted_code(s: str) -> int:
     adj = decode(s)
     return min(int(encode(adj, r), 2) if len(adj) > 1 else 0 for r in adj)
@@ -136,10 +164,11 @@ class Catalog:
     """Flattened catalogue for k colours: global shape ids run over sizes
     1..k, each size block in shape-id order."""
 
-    def __init__(self, k: int):
+    def __init__(self, k: int, skip_round: bool = False):
         if not 1 <= k <= MAX_K:
             raise ValueError("k must be in 1..8")
         self.k = k
+        self.skip_round = skip_round
         self.strings: list[str] = []
         self.size: list[int] = []
         self.local: list[int] = []
@@ -161,10 +190,28 @@ class Catalog:
                 self.right.append(-1)
                 self.beta.append(1)
                 continue
-            a, b, beta = decompose(s)
+            if skip_round and h == k:
+                d = balanced_decompose(s, k)
+                if d is None:  # not counted at level k: no decomposition
+                    self.left.append(-1)
+                    self.right.append(-1)
+                    self.beta.append(1)
+                    continue
+                a, b, beta = d
+            else:
+                a, b, beta = decompose(s)
             self.left.append(gid[(len(a) // 2 + 1, a)])
             self.right.append(gid[(len(b) // 2 + 1, b)])
             self.beta.append(beta)
+
+    def copies_divisor(self, h: int) -> list[int]:
+        """Per unrooted shape of size h: how many rooted copies the level-h
+        table holds for each copy of the tree -- h (one per node), or, at
+        level k with round skipping, a_j (0 for the star, not counted)."""
+        codes = unrooted_shapes(h)
+        if self.skip_round and h == self.k:
+            return [balanced_rootings(c, h) for c in codes]
+        return [h] * len(codes)
 
     def r(self, h: int) -> int:
         return self.first[h + 1] - self.first[h]

@@ -99,6 +99,9 @@ typedef struct {
     uint8_t *colors;
     int k, width;                 /* width: 64 or 128 */
     int zero_root;                /* level k stored at colour-0 nodes only (Section 3.4.1) */
+    int skip_round;               /* level k-1 not built; level k by balanced decompositions
+                                     (Section 3.3.2); shapes with left < 0 are not counted */
+    int64_t copies[MAXK + 1][32]; /* per unrooted shape of size h: rooted copies per copy */
     int nshape;
     int32_t *size, *local, *left, *right, *beta, *unrooted;
     int first[MAXK + 2];          /* global id of the first shape of size h */
@@ -169,6 +172,7 @@ static void *build_level_worker(void *arg)
         if (t->zero_root && h == t->k && t->colors[v] != 0) continue;
         for (int g = t->first[h]; g < t->first[h + 1]; ++g) {
             const int a = t->left[g], b = t->right[g];
+            if (a < 0) continue;                 /* not counted (round skipping) */
             const int ha = t->size[a];
             for (int q = 0; q < t->nsub[h]; ++q) {          /* |C| = h, c_v in C */
                 const unsigned C = (unsigned)t->rank_mask[h][q];
@@ -255,13 +259,16 @@ static int binom(int n, int r)
 oc_tables *oc_build(int64_t n, const int64_t *row_ptr, const uint32_t *col, const uint8_t *colors,
                     int k, int width, int nshape, const int32_t *size, const int32_t *local,
                     const int32_t *left, const int32_t *right, const int32_t *beta,
-                    const int32_t *unrooted, int nthreads, int zero_root, int *status)
+                    const int32_t *unrooted, const int32_t *copies, int nthreads, int zero_root,
+                    int skip_round, int *status)
 {
     *status = OC_INVALID;
     if (k < 1 || k > MAXK || (width != 64 && width != 128) || n < 0) return NULL;
+    if (skip_round && (k < 4 || zero_root)) return NULL;
     oc_tables *t = (oc_tables *)calloc(1, sizeof(oc_tables));
     if (!t) { *status = OC_NOMEM; return NULL; }
     t->n = n; t->k = k; t->width = width; t->nshape = nshape; t->zero_root = zero_root != 0;
+    t->skip_round = skip_round != 0;
     t->nthreads = nthreads < 1 ? 1 : nthreads;
     t->nnz = row_ptr[n];
     t->row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
@@ -281,6 +288,14 @@ oc_tables *oc_build(int64_t n, const int64_t *row_ptr, const uint32_t *col, cons
     for (int g = 0; g < nshape; ++g) t->r[size[g]]++;
     int acc = 0;
     for (int h = 1; h <= k + 1; ++h) { t->first[h] = acc; if (h <= k) acc += t->r[h]; }
+    /* copies[] lists, size after size, the rooted copies per copy of every
+     * unrooted shape (h, or a_j at a round-skipped level k) */
+    for (int h = 1, p = 0; h <= k; ++h) {
+        int nu = 0;
+        for (int g = t->first[h]; g < t->first[h + 1]; ++g) if (unrooted[g] + 1 > nu) nu = unrooted[g] + 1;
+        if (nu > 32) { oc_free(t); return NULL; }
+        for (int j = 0; j < nu; ++j) t->copies[h][j] = copies[p++];
+    }
     int cnt[MAXK + 1] = { 0 };
     for (unsigned m = 0; m < (1u << k); ++m) {       /* masks ascending */
         int p = popc(m);
@@ -297,8 +312,10 @@ oc_tables *oc_build(int64_t n, const int64_t *row_ptr, const uint32_t *col, cons
     for (int64_t v = 0; v < n; ++v) *cell(t, 1, v, 0, 1u << t->colors[v]) = 1;
 
     int st = OC_OK;
-    for (int h = 2; h <= k && st == OC_OK; ++h) st = run_pool(t, h, build_level_worker);
-    for (int h = 1; h <= k - 1 && st == OC_OK; ++h) st = run_pool(t, h, check_sums_worker);
+    for (int h = 2; h <= k && st == OC_OK; ++h)
+        if (!(t->skip_round && h == k - 1)) st = run_pool(t, h, build_level_worker);
+    for (int h = 1; h <= k - 1 && st == OC_OK; ++h)
+        if (!(t->skip_round && h == k - 1)) st = run_pool(t, h, check_sums_worker);
     *status = st;
     if (st != OC_OK) { oc_free(t); return NULL; }
     return t;
@@ -306,9 +323,14 @@ oc_tables *oc_build(int64_t n, const int64_t *row_ptr, const uint32_t *col, cons
 
 /* Level-h table in the layout [v][shape][rank of C among size-h masks],
  * each count as two uint64 words (low, high). */
+static int level_missing(const oc_tables *t, int h)
+{
+    return h < 1 || h > t->k || (t->skip_round && h == t->k - 1);
+}
+
 int oc_read_level(const oc_tables *t, int h, uint64_t *out)
 {
-    if (h < 1 || h > t->k) return OC_INVALID;
+    if (level_missing(t, h)) return OC_INVALID;
     size_t cells = (size_t)t->n * (size_t)t->r[h] * (size_t)t->nsub[h];
     for (size_t i = 0; i < cells; ++i) {
         out[2 * i] = (uint64_t)t->c[h][i];
@@ -321,7 +343,7 @@ int oc_read_level(const oc_tables *t, int h, uint64_t *out)
  * all size-h masks, in the same layout as oc_read_level (one node's block). */
 int oc_neighbor_sum(const oc_tables *t, int h, int64_t v, uint64_t *out)
 {
-    if (h < 1 || h > t->k || v < 0 || v >= t->n) return OC_INVALID;
+    if (level_missing(t, h) || v < 0 || v >= t->n) return OC_INVALID;
     for (int s = 0; s < t->r[h]; ++s)
         for (int q = 0; q < t->nsub[h]; ++q) {
             unsigned C = (unsigned)t->rank_mask[h][q];
@@ -352,18 +374,41 @@ static u128 node_total(const oc_tables *t, int h, int unrooted, int64_t v)
 }
 
 /* Rooted total R = sum_v sum_{T, C} c(T_C, v) over the shapes of size h (all,
- * or the rootings of one unrooted shape); the unrooted count is R / h, each
- * copy having h rootings -- or R itself for a zero-rooted level k, where
- * each copy is stored once, at its colour-0 node. */
+ * or the rootings of one unrooted shape); the unrooted count of shape j is
+ * R_j / h, each copy having h rootings -- or R_j itself for a zero-rooted
+ * level k, where each copy is stored once, at its colour-0 node, or R_j / a_j
+ * for a round-skipped level k, where a copy is stored once per node at
+ * which its rooting has a balanced decomposition (the star: 0, not counted).
+ * With all shapes, the unrooted count is the sum over j. */
+static int shape_total(const oc_tables *t, int h, int unrooted, u128 *R, u128 *U)
+{
+    u128 r = 0;
+    for (int64_t v = 0; v < t->n; ++v)
+        if (__builtin_add_overflow(r, node_total(t, h, unrooted, v), &r)) return OC_OVERFLOW;
+    u128 div = (t->zero_root && h == t->k) ? 1 : (u128)t->copies[h][unrooted];
+    if (div == 0) {                       /* not counted */
+        if (r != 0) return OC_INTERNAL;
+        div = 1;
+    }
+    if (r % div != 0) return OC_INTERNAL;
+    *R = r;
+    *U = r / div;
+    return OC_OK;
+}
+
 int oc_total(const oc_tables *t, int h, int unrooted, uint64_t rooted[2], uint64_t unrooted_count[2])
 {
-    if (h < 1 || h > t->k) return OC_INVALID;
-    u128 R = 0;
-    for (int64_t v = 0; v < t->n; ++v)
-        if (__builtin_add_overflow(R, node_total(t, h, unrooted, v), &R)) return OC_OVERFLOW;
-    const u128 div = (t->zero_root && h == t->k) ? 1 : (u128)h;
-    if (R % div != 0) return OC_INTERNAL;
-    u128 U = R / div;
+    if (level_missing(t, h)) return OC_INVALID;
+    u128 R = 0, U = 0;
+    int nu = 0;
+    for (int g = t->first[h]; g < t->first[h + 1]; ++g) if (t->unrooted[g] + 1 > nu) nu = t->unrooted[g] + 1;
+    for (int j = 0; j < nu; ++j) {
+        if (unrooted >= 0 && j != unrooted) continue;
+        u128 r, u;
+        int st = shape_total(t, h, j, &r, &u);
+        if (st != OC_OK) return st;
+        if (__builtin_add_overflow(R, r, &R) || __builtin_add_overflow(U, u, &U)) return OC_OVERFLOW;
+    }
     rooted[0] = (uint64_t)R; rooted[1] = (uint64_t)(R >> 64);
     unrooted_count[0] = (uint64_t)U; unrooted_count[1] = (uint64_t)(U >> 64);
     return OC_OK;
@@ -648,7 +693,7 @@ static uint32_t induced_word(const oc_tables *t, const uint32_t *nodes, int h)
 int oc_sample(const oc_tables *t, int h, int unrooted, uint64_t seed, uint64_t first_index, int64_t count,
               uint32_t *nodes, uint32_t *roots, int32_t *shapes, int32_t *classes)
 {
-    if (h < 2 || h > t->k) return OC_INVALID;
+    if (h < 2 || level_missing(t, h)) return OC_INVALID;
     int st = ensure_classes(h);
     if (st != OC_OK) return st;
     root_index ri;
@@ -659,6 +704,107 @@ int oc_sample(const oc_tables *t, int h, int unrooted, uint64_t seed, uint64_t f
         if (st == OC_OK) classes[s] = oc_class_of_word(h, induced_word(t, nodes + s * h, h));
     }
     free(ri.prefix);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uncoloured star sampling (Section 3.3.2)                                  */
+/* A uniform h-star of G: the centre v with probability C(d_v, h-1) / S,     */
+/* S = sum_v C(d_v, h-1) (step 16: X = uniform(S), v = first node whose      */
+/* inclusive prefix exceeds X), then h-1 distinct neighbours uniformly: for  */
+/* t = 0..h-2, step 17 + t draws x = uniform(d_v - t) and takes the x-th     */
+/* neighbour position, ascending, among those not yet taken.                */
+/* ------------------------------------------------------------------------ */
+#define STAR_STEP 16u
+
+static int binom_u128(int64_t d, int r, u128 *out)
+{
+    /* C(d, r) = prod_{i=1..r} (d - r + i) / i, every partial product being
+     * the integer C(d - r + i, i) */
+    if (d < r) { *out = 0; return OC_OK; }
+    u128 c = 1;
+    for (int i = 1; i <= r; ++i) {
+        if (__builtin_mul_overflow(c, (u128)(d - r + i), &c)) return OC_OVERFLOW;
+        c /= (u128)i;
+    }
+    *out = c;
+    return OC_OK;
+}
+
+int oc_star_total(const oc_tables *t, int h, uint64_t out[2])
+{
+    u128 S = 0;
+    for (int64_t v = 0; v < t->n; ++v) {
+        u128 c;
+        if (binom_u128(t->row_ptr[v + 1] - t->row_ptr[v], h - 1, &c) != OC_OK ||
+            __builtin_add_overflow(S, c, &S)) return OC_OVERFLOW;
+    }
+    out[0] = (uint64_t)S; out[1] = (uint64_t)(S >> 64);
+    return OC_OK;
+}
+
+static int star_prefix(const oc_tables *t, int h, u128 **prefix, u128 *S)
+{
+    *prefix = (u128 *)malloc(sizeof(u128) * (size_t)(t->n > 0 ? t->n : 1));
+    if (!*prefix) return OC_NOMEM;
+    u128 acc = 0;
+    for (int64_t v = 0; v < t->n; ++v) {
+        u128 c;
+        if (binom_u128(t->row_ptr[v + 1] - t->row_ptr[v], h - 1, &c) != OC_OK ||
+            __builtin_add_overflow(acc, c, &acc)) { free(*prefix); *prefix = NULL; return OC_OVERFLOW; }
+        (*prefix)[v] = acc;
+    }
+    *S = acc;
+    return OC_OK;
+}
+
+static int star_one(const oc_tables *t, int h, const u128 *prefix, u128 S, uint64_t seed, uint64_t index,
+                    uint32_t *nodes_out, uint32_t *centre_out)
+{
+    if (S == 0) return OC_INVALID;
+    u128 X = draw_below(seed, index, STAR_STEP, S);
+    int64_t lo = 0, hi = t->n - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (prefix[mid] > X) hi = mid; else lo = mid + 1;
+    }
+    const int64_t v = lo, d = t->row_ptr[v + 1] - t->row_ptr[v];
+    int64_t pos[MAXK];
+    int taken = 0;
+    for (int s = 0; s < h - 1; ++s) {
+        int64_t x = (int64_t)draw_below(seed, index, STAR_STEP + 1u + (uint32_t)s, (u128)(d - s));
+        int i = 0;
+        while (i < taken && pos[i] <= x) { ++x; ++i; }    /* skip the taken positions */
+        for (int j = taken; j > i; --j) pos[j] = pos[j - 1];
+        pos[i] = x;
+        ++taken;
+    }
+    nodes_out[0] = (uint32_t)v;
+    for (int s = 0; s < h - 1; ++s) nodes_out[1 + s] = t->col[t->row_ptr[v] + pos[s]];
+    for (int i = 1; i < h; ++i)
+        for (int j = i; j > 0 && nodes_out[j - 1] > nodes_out[j]; --j) {
+            uint32_t tmp = nodes_out[j]; nodes_out[j] = nodes_out[j - 1]; nodes_out[j - 1] = tmp;
+        }
+    *centre_out = (uint32_t)v;
+    return OC_OK;
+}
+
+/* `count` uncoloured h-stars with indices first_index..: sorted nodes, the
+ * centre and the graphlet class of each. */
+int oc_sample_stars(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t count,
+                    uint32_t *nodes, uint32_t *centres, int32_t *classes)
+{
+    if (h < 2 || h > MAXK) return OC_INVALID;
+    int st = ensure_classes(h);
+    if (st != OC_OK) return st;
+    u128 *prefix, S;
+    st = star_prefix(t, h, &prefix, &S);
+    if (st != OC_OK) return st;
+    for (int64_t s = 0; s < count && st == OC_OK; ++s) {
+        st = star_one(t, h, prefix, S, seed, first_index + (uint64_t)s, nodes + s * h, centres + s);
+        if (st == OC_OK) classes[s] = oc_class_of_word(h, induced_word(t, nodes + s * h, h));
+    }
+    free(prefix);
     return st;
 }
 
@@ -705,7 +851,7 @@ int64_t oc_spanning_trees(int h, uint32_t w)
  * classes are independent and are spread over threads. */
 typedef struct {
     int h, nshape, n_unrooted, tid, nthreads, status;
-    const int32_t *size, *local, *left, *right, *beta, *unrooted;
+    const int32_t *size, *local, *left, *right, *beta, *unrooted, *copies;
     int64_t *out;
 } sigma_job;
 
@@ -728,7 +874,7 @@ static void *sigma_worker(void *arg)
         for (int i = 0; i < h; ++i) colors[i] = (uint8_t)i;
         int st;
         oc_tables *t = oc_build(h, row_ptr, col, colors, h, 128, jb->nshape, jb->size, jb->local,
-                                jb->left, jb->right, jb->beta, jb->unrooted, 1, 0, &st);
+                                jb->left, jb->right, jb->beta, jb->unrooted, jb->copies, 1, 0, 0, &st);
         if (!t) { jb->status = st; return NULL; }
         for (int j = 0; j < jb->n_unrooted; ++j) {
             uint64_t R[2], U[2];
@@ -742,8 +888,8 @@ static void *sigma_worker(void *arg)
 }
 
 int oc_sigma_matrix(int h, int nshape, const int32_t *size, const int32_t *local, const int32_t *left,
-                    const int32_t *right, const int32_t *beta, const int32_t *unrooted, int n_unrooted,
-                    int64_t *out, int nthreads)
+                    const int32_t *right, const int32_t *beta, const int32_t *unrooted,
+                    const int32_t *copies, int n_unrooted, int64_t *out, int nthreads)
 {
     int st = ensure_classes(h);
     if (st != OC_OK) return st;
@@ -753,7 +899,7 @@ int oc_sigma_matrix(int h, int nshape, const int32_t *size, const int32_t *local
     if (nthreads > 64) nthreads = 64;
     for (int i = 0; i < nthreads; ++i) {
         jobs[i] = (sigma_job){ h, nshape, n_unrooted, i, nthreads, OC_OK, size, local, left, right,
-                               beta, unrooted, out };
+                               beta, unrooted, copies, out };
         pthread_create(&th[i], NULL, sigma_worker, &jobs[i]);
     }
     for (int i = 0; i < nthreads; ++i) {
@@ -781,21 +927,66 @@ static double inv_colorful_prob(int k, int h)
 
 static double u128_to_double(u128 x) { return (double)x; }
 
+/* Graphlets that only stars span (sigma'_i = 0) on a round-skipped level k
+ * (Section 3.3.2): n_star uncoloured h-stars, hits*_i of them spanning H_i;
+ * chi-bar*_i = hits*_i / n_star estimates g_i sigma*_i / S (sigma*_i: the
+ * spanning stars of H_i, S: the h-stars of G), so
+ * g-hat_i = ((S * hits*_i) / (sigma*_i * n_star)), with no 1/p: the stars
+ * carry no colours.  Their hits are the star hits.  With S = 0 there is no
+ * star and the estimate is 0. */
+static int star_estimates(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t n_star,
+                          const int64_t *sigma_prime, const int64_t *sigma_star, double *est, uint64_t *hits)
+{
+    const int ncls = class_count[h];
+    u128 *prefix, S;
+    int st = star_prefix(t, h, &prefix, &S);
+    if (st != OC_OK) return st;
+    uint64_t *sh = (uint64_t *)calloc((size_t)ncls, sizeof(uint64_t));
+    if (!sh) { free(prefix); return OC_NOMEM; }
+    uint32_t nodes[MAXK], centre;
+    for (int64_t s = 0; S > 0 && s < n_star && st == OC_OK; ++s) {
+        st = star_one(t, h, prefix, S, seed, first_index + (uint64_t)s, nodes, &centre);
+        if (st != OC_OK) break;
+        int cls = oc_class_of_word(h, induced_word(t, nodes, h));
+        if (cls < 0) { st = OC_INTERNAL; break; }
+        sh[cls]++;
+    }
+    free(prefix);
+    if (st == OC_OK) {
+        const double Sd = u128_to_double(S);
+        for (int i = 0; i < ncls; ++i) {
+            if (sigma_prime[i] != 0) continue;
+            hits[i] = sh[i];
+            est[i] = (S > 0 && n_star > 0 && sigma_star[i] > 0)
+                         ? (Sd * (double)sh[i]) / ((double)sigma_star[i] * (double)n_star) : 0.0;
+        }
+    }
+    free(sh);
+    return st;
+}
+
 /* Uniform sampling estimator (Section 2.2): with N samples, hits_i of them
  * spanning graphlet H_i, chi-bar_i = hits_i / N estimates E[chi_i] =
  * c_i sigma_i / t, so c-hat_i = t (hits_i / N) / sigma_i and
- * g-hat_i = c-hat_i / p, evaluated as ((t * hits_i) / (sigma_i * N)) * (1/p). */
+ * g-hat_i = c-hat_i / p, evaluated as ((t * hits_i) / (sigma_i * N)) * (1/p).
+ * On a round-skipped level k a copy of tree j is drawn with probability
+ * a_j / R (R: the rooted total), so chi-bar_i estimates c_i sigma'_i / R with
+ * sigma'_i = sum_j sigma_ij a_j, passed as `sigma`; then t is replaced by R,
+ * the graphlets with sigma'_i = 0 get 0 here and their estimate from
+ * n_star uncoloured stars (star_estimates). */
 int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t N,
-                        const int64_t *sigma, double *est, uint64_t *hits)
+                        const int64_t *sigma, int64_t n_star, const int64_t *sigma_star,
+                        double *est, uint64_t *hits)
 {
-    if (h < 2 || h > t->k || N <= 0) return OC_INVALID;
+    if (h < 2 || level_missing(t, h) || N <= 0) return OC_INVALID;
     int st = ensure_classes(h);
     if (st != OC_OK) return st;
     const int ncls = class_count[h];
+    const int skipped = t->skip_round && h == t->k;
     uint64_t R[2], U[2];
     st = oc_total(t, h, -1, R, U);
     if (st != OC_OK) return st;
-    const u128 tot = (u128)U[0] | ((u128)U[1] << 64);
+    const u128 tot = skipped ? ((u128)R[0] | ((u128)R[1] << 64)) : ((u128)U[0] | ((u128)U[1] << 64));
     for (int i = 0; i < ncls; ++i) hits[i] = 0;
     root_index ri;
     st = make_root_index(t, h, -1, &ri);
@@ -812,7 +1003,8 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
     free(ri.prefix);
     const double td = u128_to_double(tot), ip = inv_colorful_prob(t->k, h);
     for (int i = 0; i < ncls; ++i)
-        est[i] = ((td * (double)hits[i]) / ((double)sigma[i] * (double)N)) * ip;
+        est[i] = sigma[i] > 0 ? ((td * (double)hits[i]) / ((double)sigma[i] * (double)N)) * ip : 0.0;
+    if (skipped) return star_estimates(t, h, seed, first_index, n_star, sigma, sigma_star, est, hits);
     return OC_OK;
 }
 
@@ -829,6 +1021,9 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
  *  - the next treelet minimises (sum_{i covered, ascending} (sigma_ij c_i) / w_i) / t_j,
  *    ties to the smaller j;
  *  - sampling stops when every graphlet is covered or after max_samples;
+ *    on a round-skipped level k the graphlets that only stars span
+ *    (sigma'_i = 0) are left out of this and estimated from n_star
+ *    uncoloured stars (star_estimates); the star shape has t_j = 0;
  *  - sample number s (0-based) uses sample index first_index + s, whatever
  *    treelet it draws from;
  *  - the result is est_i = (c_i / w_i) * (1/p), an estimate of the number
@@ -836,10 +1031,11 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
  *    est_i = 0 when w_i = 0.
  * stats: [0] samples drawn, [1] switches, [2] graphlets covered. */
 int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t max_samples,
-                    int64_t cbar, const int64_t *sigma_ij, int n_unrooted,
+                    int64_t cbar, const int64_t *sigma_ij, int n_unrooted, int64_t n_star,
+                    const int64_t *sigma_prime, const int64_t *sigma_star,
                     double *est, uint64_t *hits, int64_t *stats)
 {
-    if (h < 2 || h > t->k || max_samples < 0 || cbar < 1) return OC_INVALID;
+    if (h < 2 || level_missing(t, h) || max_samples < 0 || cbar < 1) return OC_INVALID;
     int st = ensure_classes(h);
     if (st != OC_OK) return st;
     const int ncls = class_count[h];
@@ -862,11 +1058,15 @@ int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
     for (int j = 0; j < S; ++j)
         if (tj[j] > 0 && (cur < 0 || tj[j] > tj[cur])) cur = j;
     for (int i = 0; i < ncls; ++i) hits[i] = 0;
-    int64_t drawn = 0, switches = 0, ncov = 0;
+    int64_t drawn = 0, switches = 0, ncov = 0, target = ncls;
+    if (t->skip_round && h == t->k) {      /* graphlets only stars span are left to the stars */
+        target = 0;
+        for (int i = 0; i < ncls; ++i) target += sigma_prime[i] > 0;
+    }
     if (cur < 0) goto finish;
     uint32_t nodes[MAXK], root;
     int32_t shape;
-    while (ncov < ncls && drawn < max_samples) {
+    while (ncov < target && drawn < max_samples) {
         if (!ri[cur].prefix) { st = make_root_index(t, h, cur, &ri[cur]); if (st != OC_OK) goto done; }
         st = sample_one(t, &ri[cur], seed, first_index + (uint64_t)drawn, nodes, &root, &shape);
         if (st != OC_OK) goto done;
@@ -911,6 +1111,8 @@ finish:
     }
     stats[0] = drawn; stats[1] = switches; stats[2] = ncov;
     st = OC_OK;
+    if (t->skip_round && h == t->k)
+        st = star_estimates(t, h, seed, first_index, n_star, sigma_prime, sigma_star, est, hits);
 done:
     if (ri) for (int j = 0; j < S; ++j) free(ri[j].prefix);
     free(ri); free(tj); free(tjd); free(w); free(nj); free(covered);
