@@ -96,7 +96,7 @@ mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, voi
  * S(T'', C'', v) = sum_{u ~ v} c(T''_{C''}, u) and the disjoint-colour merge
  * c(T_C, v) = (1/beta_T) sum_{C' + C'' = C} c(T'_{C'}, v) S(T'', C'', v).
  * colors: device uint8[n] with values < k (read during the call only).
- * count_bits: 64 or 128.  flags: 0 or MC_BUILD_ZERO_ROOT.  The tables stay on the device
+ * count_bits: 64 or 128.  flags: 0, MC_BUILD_ZERO_ROOT or MC_BUILD_SKIP_ROUND.  The tables stay on the device
  * until mc_free_tables; they are immutable, so concurrent readers are safe.
  * The graph must outlive the tables. */
 /* Zero-rooting (Section 3.4.1): keep the level-k counts only at nodes of
@@ -105,6 +105,19 @@ mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, voi
  * (not h t), and sampling at h = k draws the root among colour-0 nodes, still
  * uniformly over the copies. */
 #define MC_BUILD_ZERO_ROOT 0x1u
+/* Round skipping (Section 3.3.2), k >= 4, not with zero-rooting: level k is
+ * built from a balanced decomposition -- T'' the subtree of the first root
+ * child (in s_T order) with 2..k-2 nodes, T' the rest, beta_T the root
+ * children equal to T'' -- so level k-1 is never built (its tables,
+ * totals, samples and reads are MC_E_INVALID).  Rooted k-shapes without such
+ * a child (the star rooted anywhere, every leaf rooting) are not counted:
+ * their level-k entries are 0.  A copy of tree j then appears once per node
+ * at which its rooting is counted (a_j of them; 0 for the k-star), so
+ * mc_total(k, j) returns R_j and t_j = R_j / a_j (0 for the star), and the
+ * all-shapes total returns R and sum_j t_j.  k-stars are sampled uncoloured
+ * with mc_sample_stars and estimated from those samples (star_samples in
+ * mc_estimate_params). */
+#define MC_BUILD_SKIP_ROUND 0x2u
 
 mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
                           uint32_t flags, const mc_allocator *alloc, void *stream,
@@ -175,6 +188,23 @@ mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted_shape, int
                           uint64_t seed, uint64_t first_index, int64_t count, uint32_t *nodes,
                           uint32_t *roots, int32_t *shapes, int32_t *classes, void *stream);
 
+/* Uncoloured h-stars (Section 3.3.2), 2 <= h <= 8, drawn uniformly among
+ * all h-stars of the graph: sample i takes the centre v with probability
+ * C(d_v, h-1) / S, S = sum_v C(d_v, h-1), then h-1 distinct neighbours of v
+ * uniformly.  Random numbers: counter (i_lo, i_hi, 16, attempt) gives
+ * X = uniform(S) and v is the first node whose inclusive prefix of
+ * C(d_u, h-1) exceeds X; counter (i_lo, i_hi, 17 + s, attempt), s = 0..h-2,
+ * gives x = uniform(d_v - s) and the x-th neighbour position, ascending,
+ * among those not yet taken.  Outputs (device; any may be NULL): nodes
+ * uint32[count*h] ascending, centres uint32[count], classes int32[count]
+ * (graphlet class of the induced subgraph, as for mc_sample).  The star
+ * index (16 bytes per node and h) is built on first use and kept with the
+ * graph.  MC_E_INVALID when the graph has no h-star, MC_E_OVERFLOW when S
+ * does not fit in 128 bits. */
+mc_status mc_star_total(const mc_graph *g, int h, uint64_t total[2], void *stream);
+mc_status mc_sample_stars(const mc_graph *g, int h, uint64_t seed, uint64_t first_index, int64_t count,
+                          uint32_t *nodes, uint32_t *centres, int32_t *classes, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Estimation (Section 2.2 uniform; Algorithm AGS, Section 4.1)              */
 /* ------------------------------------------------------------------------ */
@@ -191,6 +221,11 @@ typedef struct {
     double eps, delta;     /* AGS accuracy, used when cbar <= 0 */
     int64_t batch;         /* AGS speculative batch; <= 0: automatic */
     int64_t node_lo, node_hi;  /* root nodes [node_lo, node_hi); node_hi <= 0: all nodes */
+    int64_t star_samples;  /* round-skipped tables at h = k: uncoloured h-stars drawn (with the
+                              same sample indices) to estimate the graphlets that only stars
+                              span; their estimate is (S * hits*_i) / (sigma*_i * star_samples),
+                              S the h-stars of G, sigma*_i the spanning stars of H_i, and their
+                              hits are the star hits (0 star samples: estimate 0) */
 } mc_estimate_params;
 
 typedef struct {

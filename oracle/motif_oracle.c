@@ -589,13 +589,25 @@ static uint32_t relabel_word(uint32_t w, int h, const int *p)
     return out;
 }
 
+/* The smallest relabelled word over all h! permutations.  The adjacency
+ * matrix of w and the bit position of every pair are read out once, so each
+ * permutation costs one table lookup per pair (the same minimum as taking
+ * relabel_word for every permutation). */
 uint32_t oc_canonical_code(int h, uint32_t w)
 {
-    int p[MAXK];
+    int p[MAXK], bit[MAXK][MAXK], adj[MAXK][MAXK];
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) {
+            bit[i][j] = i < j ? pair_bit(h, i, j) : 0;
+            adj[i][j] = i != j && word_has_edge(w, h, i, j);
+        }
     for (int i = 0; i < h; ++i) p[i] = i;
     uint32_t best = w;
     do {
-        uint32_t x = relabel_word(w, h, p);
+        uint32_t x = 0;
+        for (int i = 0; i < h; ++i)
+            for (int j = i + 1; j < h; ++j)
+                if (adj[p[i]][p[j]]) x |= 1u << bit[i][j];
         if (x < best) best = x;
     } while (next_perm(p, h));
     return best;

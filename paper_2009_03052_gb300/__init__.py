@@ -25,6 +25,7 @@ MC_OK, MC_E_INVALID, MC_E_NOMEM, MC_E_OVERFLOW, MC_E_CUDA, MC_E_TIMEOUT, MC_E_UN
 MC_GRAPH_DEVICE_PTRS = 1
 MC_GRAPH_TRUSTED = 2
 MC_BUILD_ZERO_ROOT = 1
+MC_BUILD_SKIP_ROUND = 2
 MC_REQ_SAMPLE = 0
 MC_REQ_ESTIMATE = 1
 MC_EST_UNIFORM = 0
@@ -37,7 +38,7 @@ EXPORTED = [
     "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
     "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
-    "mc_server_wait", "mc_server_free",
+    "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars",
 ]
 
 
@@ -61,7 +62,7 @@ class EstimateParams(C.Structure):
     _fields_ = [("mode", C.c_int), ("h", C.c_int), ("seed", C.c_uint64),
                 ("first_index", C.c_uint64), ("samples", C.c_int64), ("cbar", C.c_int64),
                 ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64),
-                ("node_lo", C.c_int64), ("node_hi", C.c_int64)]
+                ("node_lo", C.c_int64), ("node_hi", C.c_int64), ("star_samples", C.c_int64)]
 
 
 class Request(C.Structure):
@@ -121,6 +122,8 @@ def load(path: str | None = None):
                                        C.POINTER(C.c_double)]
         lib.mc_server_free.argtypes = [P]
         lib.mc_server_free.restype = None
+        lib.mc_star_total.argtypes = [P, C.c_int, P, P]
+        lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
         _lib = lib
         return lib
 
@@ -225,6 +228,23 @@ class Graph:
     def from_csr(cls, g, **kw) -> "Graph":
         return cls(g.row_ptr, g.col, **kw)
 
+    def star_total(self, h: int, stream=None) -> int:
+        """mc_star_total: the number of h-stars, sum_v C(d_v, h-1)."""
+        out = (C.c_uint64 * 2)()
+        _check(load().mc_star_total(self.handle, h, out, _stream_ptr(stream)))
+        return int(out[0]) | (int(out[1]) << 64)
+
+    def sample_stars(self, h: int, seed: int, first_index: int, count: int, stream=None):
+        """mc_sample_stars: uncoloured uniform h-stars, device tensors
+        (nodes [count, h], centres, classes)."""
+        torch = _torch()
+        t_nodes = torch.empty((max(count, 1), h), dtype=torch.int32, device="cuda")
+        t_cen = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
+        t_cls = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
+        _check(load().mc_sample_stars(self.handle, h, seed, first_index, count, _ptr(t_nodes),
+                                      _ptr(t_cen), _ptr(t_cls), _stream_ptr(stream)))
+        return t_nodes[:count], t_cen[:count], t_cls[:count]
+
     def info(self) -> tuple[int, int, int]:
         n, nnz, md = C.c_int64(), C.c_int64(), C.c_int64()
         _check(load().mc_graph_info(self.handle, C.byref(n), C.byref(nnz), C.byref(md)))
@@ -255,7 +275,8 @@ class Tables:
     """mc_build_tables: the exact colourful treelet count tables."""
 
     def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None,
-                 zero_root: bool = False, own_memory: bool = False, _handle=None):
+                 zero_root: bool = False, own_memory: bool = False, skip_round: bool = False,
+                 _handle=None):
         torch = _torch()
         if _handle is not None:  # built by batch()
             self.graph, self.k, self.bits, self._alloc, self.handle = graph, k, count_bits, \
@@ -268,8 +289,9 @@ class Tables:
         h = C.c_void_p()
         # own_memory: the library allocates (stream-ordered scratch, no
         # callbacks into Python), e.g. for tables served from worker threads
+        flags = (MC_BUILD_ZERO_ROOT if zero_root else 0) | (MC_BUILD_SKIP_ROUND if skip_round else 0)
         _check(load().mc_build_tables(graph.handle, _ptr(colors) if graph.n else None, k,
-                                      count_bits, MC_BUILD_ZERO_ROOT if zero_root else 0,
+                                      count_bits, flags,
                                       None if own_memory else C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
@@ -350,13 +372,13 @@ class Tables:
 
     def estimate(self, h: int, seed: int, samples: int, mode: int = MC_EST_UNIFORM,
                  first_index: int = 0, cbar: int = 0, eps: float = 0.0, delta: float = 0.0,
-                 batch: int = 0, node_range=(0, 0), stream=None):
+                 batch: int = 0, node_range=(0, 0), star_samples: int = 0, stream=None):
         """mc_estimate_counts: (estimates, hits, stats dict)."""
         ncls = num_classes(h)
         est = np.zeros(ncls, np.float64)
         hits = np.zeros(ncls, np.uint64)
         prm = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
-                             node_range[0], node_range[1])
+                             node_range[0], node_range[1], star_samples)
         st = EstimateStats()
         _check(load().mc_estimate_counts(self.handle, C.byref(prm), _ptr(est), _ptr(hits),
                                          C.byref(st), _stream_ptr(stream)))
@@ -482,9 +504,9 @@ class Server:
     def submit_estimate(self, table: int, h: int, seed: int, samples: int,
                         mode: int = MC_EST_UNIFORM, first_index: int = 0, cbar: int = 0,
                         eps: float = 0.0, delta: float = 0.0, batch: int = 0,
-                        node_range=(0, 0)) -> int:
+                        node_range=(0, 0), star_samples: int = 0) -> int:
         e = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
-                           node_range[0], node_range[1])
+                           node_range[0], node_range[1], star_samples)
         r = Request(MC_REQ_ESTIMATE, table, 0, -1, 0, 0, 0, 0, 0, e)
         i = C.c_int64()
         _check(load().mc_server_submit(self.handle, C.byref(r), C.byref(i)))

@@ -686,6 +686,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
     ma.n = n;
     ma.err = err;
     for (int h = 2; h <= k; ++h) {
+        if (t->skip_round && h == k - 1) continue;  // round k-1 skipped: nothing reads it
         ma.info = t->m_info[h];
         ma.off = t->m_off[h];
         ma.terms = t->m_terms[h];
@@ -741,13 +742,18 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         MC_REQUIRE(colors || g->n == 0, "colors is NULL");
         if (k < 2 || k > MAXK) throw Error(MC_E_UNSUPPORTED, "k must be in 2..8");
         MC_REQUIRE(count_bits == 64 || count_bits == 128, "count_bits must be 64 or 128");
-        MC_REQUIRE((flags & ~MC_BUILD_ZERO_ROOT) == 0, "unknown flags");
+        MC_REQUIRE((flags & ~(MC_BUILD_ZERO_ROOT | MC_BUILD_SKIP_ROUND)) == 0, "unknown flags");
+        if (flags & MC_BUILD_SKIP_ROUND) {
+            MC_REQUIRE(k >= 4, "round skipping needs k >= 4");
+            MC_REQUIRE(!(flags & MC_BUILD_ZERO_ROOT), "round skipping and zero-rooting do not combine");
+        }
         cudaStream_t s = (cudaStream_t)stream;
         t = new mc_tables();
         t->g = g;
         t->k = k;
         t->bits = count_bits;
         t->zero_root = flags & MC_BUILD_ZERO_ROOT;
+        t->skip_round = flags & MC_BUILD_SKIP_ROUND;
         t->geo = make_geometry(k);
         t->arena.stream = s;
         if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
@@ -773,8 +779,10 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
 
         }
         // programs
-        const Programs &P = programs(k);
+        const Programs &P = programs(k, t->skip_round);
+        for (int j = 0; j < 32; ++j) t->copies_k[j] = P.copies[j];
         for (int h = 2; h <= k; ++h) {
+            if (t->level_missing(h)) continue;
             const MergeLevel &M = P.merge[h];
             t->m_info[h] = t->arena.get<int32_t>(M.info.size());
             t->m_off[h] = t->arena.get<int32_t>(M.offset.size());
@@ -784,14 +792,18 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
             MC_CUDA(cudaMemcpyAsync(t->m_terms[h], M.terms.data(), M.terms.size() * 4, cudaMemcpyHostToDevice, s));
         }
         for (int h = 1; h <= k - 1; ++h) {
+            if (t->level_missing(h)) continue;
             const GatherLevel &L = P.gather[h];
             t->g_map[h] = t->arena.get<int16_t>(L.map.size());
             MC_CUDA(cudaMemcpyAsync(t->g_map[h], L.map.data(), L.map.size() * 2, cudaMemcpyHostToDevice, s));
         }
         // tables
-        for (int h = 2; h <= k; ++h) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
-        for (int h = 1; h <= k - 1; ++h) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
-        for (int h = 2; h <= k - 1; ++h) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
+        for (int h = 2; h <= k; ++h)
+            if (!t->level_missing(h)) t->c[h] = t->arena.get<uint8_t>((size_t)n * G.Wc[h] * cb);
+        for (int h = 1; h <= k - 1; ++h)
+            if (!t->level_missing(h)) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
+        for (int h = 2; h <= k - 1; ++h)
+            if (!t->level_missing(h)) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
 
         if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
         else build_levels<u128>(t, err, scratch, s);
@@ -827,6 +839,7 @@ void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
     mc_tables *t = const_cast<mc_tables *>(tc);
     std::lock_guard<std::mutex> lock(t->idx_mu);
     if (t->prefix[h] || h < 2) return;
+    if (t->level_missing(h)) throw Error(MC_E_INVALID, "level h was skipped (round skipping)");
     const int64_t n = t->g->n;
     Arena scratch(true);
     scratch.alloc = t->arena.alloc;
@@ -862,58 +875,90 @@ extern "C" void mc_free_tables(mc_tables *t)
     mc_free_graph(owned);
 }
 
+// Rooted total R of level h over the nodes [lo, hi): all shapes (j < 0,
+// from the cached root index) or the rootings of unrooted shape j.
+static u128 level_rooted_total(const mc_tables *t, int h, int j, int64_t lo, int64_t hi, cudaStream_t s)
+{
+    const ShapeCatalog &cat = shape_catalog();
+    const int64_t n = t->g->n;
+    if (h == 1) return j > 0 ? 0 : (u128)(hi - lo);
+    if (hi <= lo) return 0;
+    // the level's node prefix, read at the range's ends
+    const u128 *pre = nullptr;
+    Arena scratch(true);
+    scratch.alloc = t->arena.alloc;
+    scratch.stream = s;
+    int *err = scratch.get<int>(1);
+    MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (j < 0) {
+        ensure_level_index(t, h, s);
+        pre = t->prefix[h];
+    } else {
+        uint64_t a0 = 0, a1 = 0;
+        for (int i = 0; i < cat.r[h]; ++i)
+            if (cat.shapes[cat.gid(h, i)].unrooted == j) {
+                if (i < 64) a0 |= 1ull << i; else a1 |= 1ull << (i - 64);
+            }
+        u128 *tot = scratch.get<u128>((size_t)n);
+        launch_row_totals(t, h, a0, a1, tot, err, s);
+        inclusive_scan_u128(tot, n, err, scratch, s);
+        pre = tot;
+    }
+    u128 top = 0, base = 0;
+    int herr = 0;
+    MC_CUDA(cudaMemcpyAsync(&top, pre + (hi - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    if (lo > 0) MC_CUDA(cudaMemcpyAsync(&base, pre + (lo - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error(MC_E_OVERFLOW, "level total does not fit in 128 bits");
+    return top - base;
+}
+
+// Copies of unrooted shape j from its rooted total: R / h (one rooted copy
+// per node), R at a zero-rooted level k, R / a_j at a round-skipped level k
+// (a_j = 0: the star, not counted).
+static u128 unrooted_from_rooted(const mc_tables *t, int h, int j, u128 R)
+{
+    u128 div = (u128)t->copies_div(h);
+    if (t->skip_round && h == t->k) {
+        div = (u128)t->copies_k[j];
+        if (div == 0) {
+            if (R != 0) throw Error(MC_E_INTERNAL, "an uncounted shape has counts");
+            return 0;
+        }
+    }
+    if (R % div != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
+    return R / div;
+}
+
 extern "C" mc_status mc_total_range(const mc_tables *t, int h, int32_t unrooted_shape, int64_t node_lo,
                                     int64_t node_hi, uint64_t rooted[2], uint64_t unrooted_count[2], void *stream)
 {
     return guarded([&] {
         MC_REQUIRE(t && rooted && unrooted_count, "NULL argument");
         MC_REQUIRE(h >= 1 && h <= t->k, "h must be in 1..k");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         const ShapeCatalog &cat = shape_catalog();
-        MC_REQUIRE(unrooted_shape < cat.n_unrooted[h], "unrooted shape out of range");
+        MC_REQUIRE(unrooted_shape >= -1 && unrooted_shape < cat.n_unrooted[h], "unrooted shape out of range");
         const int64_t n = t->g->n;
         int64_t lo = node_lo, hi = node_hi;
         if (hi <= 0 && lo <= 0) { lo = 0; hi = n; }
         if (hi <= 0) hi = n;
         MC_REQUIRE(lo >= 0 && lo <= hi && hi <= n, "node range out of bounds");
         cudaStream_t s = (cudaStream_t)stream;
-        u128 R = 0;
-        if (h == 1) {
-            R = unrooted_shape > 0 ? 0 : (u128)(hi - lo);
-        } else if (hi > lo) {
-            // the level's node prefix (all shapes: the cached root index; one
-            // unrooted shape: computed here), read at the range's ends
-            const u128 *pre = nullptr;
-            Arena scratch(true);
-            scratch.alloc = t->arena.alloc;
-            scratch.stream = s;
-            int *err = scratch.get<int>(1);
-            MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-            if (unrooted_shape < 0) {
-                ensure_level_index(t, h, s);
-                pre = t->prefix[h];
-            } else {
-                uint64_t a0 = 0, a1 = 0;
-                for (int i = 0; i < cat.r[h]; ++i)
-                    if (cat.shapes[cat.gid(h, i)].unrooted == unrooted_shape) {
-                        if (i < 64) a0 |= 1ull << i; else a1 |= 1ull << (i - 64);
-                    }
-                u128 *tot = scratch.get<u128>((size_t)n);
-                launch_row_totals(t, h, a0, a1, tot, err, s);
-                inclusive_scan_u128(tot, n, err, scratch, s);
-                pre = tot;
-            }
-            u128 top = 0, base = 0;
-            int herr = 0;
-            MC_CUDA(cudaMemcpyAsync(&top, pre + (hi - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
-            if (lo > 0) MC_CUDA(cudaMemcpyAsync(&base, pre + (lo - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
-            MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-            MC_CUDA(cudaStreamSynchronize(s));
-            if (herr) throw Error(MC_E_OVERFLOW, "level total does not fit in 128 bits");
-            R = top - base;
+        const u128 R = level_rooted_total(t, h, unrooted_shape, lo, hi, s);
+        u128 U = 0;
+        if (unrooted_shape >= 0) {
+            U = unrooted_from_rooted(t, h, unrooted_shape, R);
+        } else if (t->skip_round && h == t->k) {
+            // per-shape divisors differ: t = sum_j R_j / a_j
+            for (int j = 0; j < cat.n_unrooted[h]; ++j)
+                U += unrooted_from_rooted(t, h, j, level_rooted_total(t, h, j, lo, hi, s));
+        } else {
+            const u128 div = (u128)t->copies_div(h);
+            if (R % div != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
+            U = R / div;
         }
-        const u128 div = (u128)t->copies_div(h);
-        if (R % div != 0) throw Error(MC_E_INTERNAL, "rooted total not divisible by h");
-        const u128 U = R / div;
         rooted[0] = (uint64_t)R;
         rooted[1] = (uint64_t)(R >> 64);
         unrooted_count[0] = (uint64_t)U;
@@ -998,6 +1043,7 @@ extern "C" mc_status mc_table_layout(const mc_tables *t, int h, int which, int64
         MC_REQUIRE(t, "tables is NULL");
         MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
         MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         if (row_entries) *row_entries = which ? t->geo.Ws[h] : t->geo.Wc[h];
         if (entry_bytes) *entry_bytes = t->bits / 8;
     });
@@ -1010,6 +1056,7 @@ extern "C" mc_status mc_read_table(const mc_tables *t, int h, int which, void *d
         MC_REQUIRE(t && dst, "NULL argument");
         MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
         MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         const int64_t W = which ? t->geo.Ws[h] : t->geo.Wc[h];
         const size_t bytes = (size_t)t->g->n * W * (t->bits / 8);
         MC_REQUIRE(dst_bytes >= bytes, "dst too small");

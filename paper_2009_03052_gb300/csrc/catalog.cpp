@@ -183,18 +183,79 @@ Geometry make_geometry(int k)
     return g;
 }
 
-static Programs build_programs(int k)
+static int shape_gid(const ShapeCatalog &cat, const std::string &str)
+{
+    const int h = (int)str.size() / 2 + 1;
+    for (int i = 0; i < cat.r[h]; ++i)
+        if (cat.shapes[cat.gid(h, i)].str == str) return cat.gid(h, i);
+    return -1;
+}
+
+// balanced decomposition of a rooted k-shape: false when none exists
+static bool balanced(const ShapeCatalog &cat, const std::string &str, int k, int &left, int &right, int &beta)
+{
+    const std::vector<std::string> bl = blocks_of(str);
+    for (size_t i = 0; i < bl.size(); ++i) {
+        const int sz = (int)bl[i].size() / 2;
+        if (sz < 2 || sz > k - 2) continue;
+        std::string rest;
+        for (size_t j = 0; j < bl.size(); ++j)
+            if (j != i) rest += bl[j];
+        left = shape_gid(cat, rest);
+        right = shape_gid(cat, bl[i].substr(1, bl[i].size() - 2));
+        beta = (int)std::count(bl.begin(), bl.end(), bl[i]);
+        return true;
+    }
+    return false;
+}
+
+static Programs build_programs(int k, bool skip)
 {
     const ShapeCatalog &cat = shape_catalog();
     Programs P;
     P.geo = make_geometry(k);
+    P.skip = skip;
     const Geometry &G = P.geo;
+    for (int i = 0; i < MAX_SHAPES; ++i) P.bal_left[i] = P.bal_right[i] = -1, P.bal_beta[i] = 1;
+    for (int j = 0; j < 32; ++j) P.copies[j] = k;
+    if (skip) {
+        for (int s = 0; s < cat.r[k]; ++s) {
+            const int g = cat.gid(k, s);
+            int l, r, b;
+            if (balanced(cat, cat.shapes[g].str, k, l, r, b)) P.bal_left[g] = l, P.bal_right[g] = r, P.bal_beta[g] = b;
+        }
+        // a_j: nodes of tree j at which its rooting has a balanced decomposition
+        for (int j = 0; j < cat.n_unrooted[k]; ++j) {
+            int rep = -1;
+            for (int s = 0; s < cat.r[k] && rep < 0; ++s)
+                if (cat.shapes[cat.gid(k, s)].unrooted == j) rep = cat.gid(k, s);
+            const auto adj = tree_adjacency(cat.shapes[rep].str);
+            int a = 0;
+            for (int x = 0; x < (int)adj.size(); ++x) {
+                int l, r, b;
+                a += balanced(cat, rooted_string(adj, x, -1), k, l, r, b) ? 1 : 0;
+            }
+            P.copies[j] = a;
+        }
+    }
     for (int h = 2; h <= k; ++h) {
+        if (skip && h == k - 1) continue;
         MergeLevel &M = P.merge[h];
         for (int s = 0; s < cat.r[h]; ++s) {
             const Shape &T = cat.shapes[cat.gid(h, s)];
-            const Shape &A = cat.shapes[T.left];
-            const Shape &B = cat.shapes[T.right];
+            int left = T.left, right = T.right, beta = T.beta;
+            if (skip && h == k) {
+                left = P.bal_left[cat.gid(h, s)], right = P.bal_right[cat.gid(h, s)], beta = P.bal_beta[cat.gid(h, s)];
+                if (left < 0) {  // not counted: no terms
+                    for (int rho = 0; rho < G.Bc[h]; ++rho) {
+                        M.offset.push_back((int32_t)M.terms.size());
+                        M.info.push_back(1 | (1 << 4) | (1 << 8));
+                    }
+                    continue;
+                }
+            }
+            const Shape &A = cat.shapes[left];
+            const Shape &B = cat.shapes[right];
             const int h1 = A.size, h2 = B.size;
             for (int rho = 0; rho < G.Bc[h]; ++rho) {
                 // D: the h-1 colours of C other than c_v, as a relative set
@@ -211,11 +272,12 @@ static Programs build_programs(int k)
                     }
                     if (sub == 0) break;
                 }
-                M.info.push_back(h1 | (h2 << 4) | (T.beta << 8) | (nterms << 16));
+                M.info.push_back(h1 | (h2 << 4) | (beta << 8) | (nterms << 16));
             }
         }
     }
     for (int h = 1; h <= k - 1; ++h) {
+        if (skip && h == k - 1) continue;
         GatherLevel &L = P.gather[h];
         L.map.assign((size_t)k * k * G.Bs[h], -1);
         for (int cv = 0; cv < k; ++cv)
@@ -235,12 +297,12 @@ static Programs build_programs(int k)
     return P;
 }
 
-const Programs &programs(int k)
+const Programs &programs(int k, bool skip)
 {
-    static Programs cache[MAXK + 1];
-    static std::once_flag once[MAXK + 1];
-    std::call_once(once[k], [k] { cache[k] = build_programs(k); });
-    return cache[k];
+    static Programs cache[2][MAXK + 1];
+    static std::once_flag once[2][MAXK + 1];
+    std::call_once(once[skip][k], [k, skip] { cache[skip][k] = build_programs(k, skip); });
+    return cache[skip][k];
 }
 
 }  // namespace mc

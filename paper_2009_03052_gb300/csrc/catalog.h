@@ -66,11 +66,21 @@ struct GatherLevel {
     std::vector<int16_t> map;
 };
 
+// With round skipping (Section 3.3.2) level k is built from a balanced
+// decomposition: T'' is the subtree of the first root child (in s_T order)
+// with 2..k-2 nodes, T' the rest, beta the number of root children equal
+// to T''; level k-1 is never built.  Rooted k-shapes without such a child
+// (star and leaf rootings) are not counted: their merge has no terms.
 struct Programs {
     Geometry geo;
     MergeLevel merge[MAXK + 1];
     GatherLevel gather[MAXK + 1];
+    bool skip = false;
+    int bal_left[MAX_SHAPES], bal_right[MAX_SHAPES], bal_beta[MAX_SHAPES];  // per level-k shape (global
+                                                                             // ids; -1: not counted)
+    int copies[32];  // per unrooted k-shape: rooted copies the level-k table holds per copy
+                     // (k, or with skipping a_j, the balanced rootings; 0 for the star)
 };
-const Programs &programs(int k);
+const Programs &programs(int k, bool skip = false);
 
 }  // namespace mc

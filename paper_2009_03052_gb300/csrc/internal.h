@@ -140,6 +140,11 @@ struct mc_graph {
     int64_t *hub_chunk0 = nullptr;  // n_hubs + 1 entries
     int32_t *node_chunk0 = nullptr; // per node: its first chunk if it is a hub, else -1
     mc::Arena arena;
+    // uncoloured h-star index, built on first use: inclusive prefix over v of
+    // C(d_v, h-1) and its total
+    std::mutex star_mu;
+    mc::u128 *star_prefix[mc::MAXK + 1] = {nullptr};
+    mc::u128 star_total[mc::MAXK + 1] = {0};
 };
 
 struct mc_tables {
@@ -149,6 +154,9 @@ struct mc_tables {
     bool zero_root = false;  // level k stored at colour-0 nodes only
     // copies per stored level-h entry sum: h, or 1 for a zero-rooted level k
     int copies_div(int h) const { return (zero_root && h == k) ? 1 : h; }
+    bool skip_round = false;  // level k-1 skipped, level k by balanced decompositions
+    int copies_k[32] = {0};   // with skip_round: a_j per unrooted k-shape (0: the star)
+    bool level_missing(int h) const { return h < 1 || h > k || (skip_round && h == k - 1); }
     mc::Geometry geo;
     uint8_t *colors = nullptr;                 // device uint8[n]
     uint8_t *ecol = nullptr;                   // device uint8[nnz]: colour of col[e]

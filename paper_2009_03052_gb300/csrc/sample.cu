@@ -776,10 +776,121 @@ __global__ void uniform_estimate_kernel(const unsigned long long *hits, const in
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncls) return;
+    if (sigma[i] <= 0) { est[i] = 0.0; return; }  // graphlets no counted tree spans
     const double td = u128_to_double(t);
     const double num = __dmul_rn(td, __ull2double_rn(hits[i]));
     const double den = __dmul_rn(__ll2double_rn(sigma[i]), __ll2double_rn(N));
     est[i] = __dmul_rn(__ddiv_rn(num, den), inv_p);
+}
+
+// ---------------------------------------------------------------------------
+// Uncoloured star sampling (Section 3.3.2).  Node weights C(d_v, h-1), their
+// inclusive prefix, then one thread per sample: the centre by a binary
+// search of the prefix, the leaves by sequential selection without
+// replacement (the x-th untaken position, x = uniform(d_v - s)).
+// ---------------------------------------------------------------------------
+constexpr uint32_t STAR_STEP = 16;
+
+// q = x / d for a small divisor, by 32-bit long division
+__device__ __forceinline__ u128 div_small(u128 x, uint32_t d)
+{
+    u128 q = 0;
+    uint64_t r = 0;
+    for (int i = 3; i >= 0; --i) {
+        const uint64_t cur = (r << 32) | (uint32_t)(x >> (32 * i));
+        q |= (u128)(cur / d) << (32 * i);
+        r = cur % d;
+    }
+    return q;
+}
+
+__global__ void star_weights_kernel(const int64_t *__restrict__ row_ptr, int64_t n, int r, u128 *__restrict__ w,
+                                    int *err)
+{
+    bool ovf = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        u128 c = d >= r ? 1 : 0;
+        // C(d, r) = prod_{i=1..r} (d - r + i) / i; each partial product is
+        // i * C(d - r + i, i), so every division is exact
+        for (int i = 1; i <= r && c; ++i) {
+            u128 p;
+            ovf |= mul_ovf(c, (u128)(d - r + i), p);
+            c = div_small(p, (uint32_t)i);
+        }
+        w[v] = c;
+    }
+    if (ovf) atomicOr(err, 1);
+}
+
+struct StarArgs {
+    const int64_t *row_ptr;
+    const uint32_t *col;
+    const u128 *prefix;
+    int64_t n;
+    u128 S;
+    int h;
+    uint64_t seed, first_index;
+    int64_t count;
+    const uint16_t *lut;
+    uint32_t *nodes, *centres;
+    int32_t *classes;
+    unsigned long long *hist;
+    int *err;
+};
+
+__global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarArgs a)
+{
+    bool bad = false;
+    const int h = a.h;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t idx = a.first_index + (uint64_t)i;
+        u128 X;
+        if (!draw_below(a.seed, idx, STAR_STEP, a.S, X)) { bad = true; continue; }
+        int64_t lo = 0, hi = a.n - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.prefix[mid] > X) hi = mid; else lo = mid + 1;
+        }
+        const int64_t v = lo, e0 = a.row_ptr[v];
+        const uint64_t d = (uint64_t)(a.row_ptr[v + 1] - e0);
+        uint64_t pos[MAXK];
+        int taken = 0;
+        for (int s = 0; s < h - 1; ++s) {
+            uint64_t x;
+            if (!draw_below(a.seed, idx, STAR_STEP + 1 + (uint32_t)s, d - (uint64_t)s, x)) { bad = true; break; }
+            int j = 0;
+            while (j < taken && pos[j] <= x) { ++x; ++j; }  // skip the positions taken
+            for (int q = taken; q > j; --q) pos[q] = pos[q - 1];
+            pos[j] = x;
+            ++taken;
+        }
+        if (taken != h - 1) continue;
+        // the centre among its leaves, ascending (leaves ascend with position)
+        uint32_t nd[MAXK];
+        int m = 0;
+        bool placed = false;
+        const uint32_t c = (uint32_t)v;
+        for (int s = 0; s < h - 1; ++s) {
+            const uint32_t u = a.col[e0 + (int64_t)pos[s]];
+            if (!placed && c < u) { nd[m++] = c; placed = true; }
+            nd[m++] = u;
+        }
+        if (!placed) nd[m++] = c;
+        uint32_t word = 0;
+        for (int x = 0; x < h; ++x)
+            for (int y = x + 1; y < h; ++y)
+                if (nd[x] == c || nd[y] == c || adjacent(a.row_ptr, a.col, nd[x], nd[y]))
+                    word |= 1u << pair_pos(h, x, y);
+        const int cls = a.lut[word];
+        if (cls == 0xffff) bad = true;
+        if (a.nodes) for (int x = 0; x < h; ++x) a.nodes[i * h + x] = nd[x];
+        if (a.centres) a.centres[i] = c;
+        if (a.classes) a.classes[i] = cls == 0xffff ? -1 : cls;
+        if (a.hist && cls != 0xffff) atomicAdd(&a.hist[cls], 1ull);
+    }
+    if (bad) atomicOr(a.err, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -817,6 +928,14 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
         a.lft[gid] = (uint8_t)std::max(s.left, 0);
         a.rgt[gid] = (uint8_t)std::max(s.right, 0);
         a.beta[gid] = (uint8_t)s.beta;
+    }
+    if (t->skip_round) {  // level k descends by its balanced decompositions
+        const Programs &P = programs(t->k, true);
+        for (int gid = cat.first[t->k]; gid < cat.first[t->k + 1]; ++gid) {
+            a.lft[gid] = (uint8_t)std::max(P.bal_left[gid], 0);
+            a.rgt[gid] = (uint8_t)std::max(P.bal_right[gid], 0);
+            a.beta[gid] = (uint8_t)P.bal_beta[gid];
+        }
     }
     for (unsigned m = 0; m < (1u << (t->k - 1)); ++m) a.crank[m] = (uint8_t)colex_rank(m);
     for (int m = 0; m < MAXK; ++m)
@@ -1010,6 +1129,7 @@ extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted
     return guarded([&] {
         MC_REQUIRE(t, "tables is NULL");
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         MC_REQUIRE(count >= 0, "count must be >= 0");
         MC_REQUIRE(unrooted_shape < shape_catalog().n_unrooted[h], "unrooted shape out of range");
         if (count == 0) return;
@@ -1050,12 +1170,145 @@ extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted
     });
 }
 
+// the star index of size h (built once per graph)
+static u128 ensure_star_index(const mc_graph *gc, int h, cudaStream_t s)
+{
+    mc_graph *g = const_cast<mc_graph *>(gc);
+    std::lock_guard<std::mutex> lock(g->star_mu);
+    if (g->star_prefix[h]) return g->star_total[h];
+    const int64_t n = g->n;
+    Arena scratch(true);
+    scratch.alloc = g->arena.alloc;
+    scratch.stream = s;
+    int *err = scratch.get<int>(1);
+    MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    u128 *p = g->arena.get<u128>((size_t)std::max<int64_t>(n, 1));
+    u128 S = 0;
+    int herr = 0;
+    if (n) {
+        MC_LAUNCH("star_weights", s, star_weights_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->row_ptr, n, h - 1, p, err));
+        inclusive_scan_u128(p, n, err, scratch, s);
+        MC_CUDA(cudaMemcpyAsync(&S, p + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+    }
+    MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error(MC_E_OVERFLOW, "the number of stars does not fit in 128 bits");
+    g->star_total[h] = S;
+    g->star_prefix[h] = p;  // published last
+    return S;
+}
+
+// `count` stars from index first_index into the given outputs and/or a
+// class histogram (device)
+static void run_stars(const mc_graph *g, int h, uint64_t seed, uint64_t first_index, int64_t count,
+                      uint32_t *nodes, uint32_t *centres, int32_t *classes, unsigned long long *hist,
+                      Arena &scratch, cudaStream_t s)
+{
+    const u128 S = ensure_star_index(g, h, s);
+    if (S == 0) throw Error(MC_E_INVALID, "the graph has no star of this size");
+    const ClassCatalog *cc = class_catalog(h);
+    int *err = scratch.get<int>(1);
+    MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    StarArgs a{};
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.prefix = g->star_prefix[h];
+    a.n = g->n;
+    a.S = S;
+    a.h = h;
+    a.seed = seed;
+    a.first_index = first_index;
+    a.count = count;
+    a.lut = cc->lut;
+    a.nodes = nodes;
+    a.centres = centres;
+    a.classes = classes;
+    a.hist = hist;
+    a.err = err;
+    MC_LAUNCH("star_sample", s, star_kernel<<<grid_for(count, 256), 256, 0, s>>>(a));
+    int herr = 0;
+    MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error(MC_E_INTERNAL, "star sampler consistency check failed");
+}
+
+extern "C" mc_status mc_star_total(const mc_graph *g, int h, uint64_t total[2], void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(g && total, "NULL argument");
+        MC_REQUIRE(h >= 2 && h <= MAXK, "h must be in 2..8");
+        const u128 S = ensure_star_index(g, h, (cudaStream_t)stream);
+        total[0] = (uint64_t)S;
+        total[1] = (uint64_t)(S >> 64);
+    });
+}
+
+extern "C" mc_status mc_sample_stars(const mc_graph *g, int h, uint64_t seed, uint64_t first_index, int64_t count,
+                                     uint32_t *nodes, uint32_t *centres, int32_t *classes, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(g, "graph is NULL");
+        MC_REQUIRE(h >= 2 && h <= MAXK, "h must be in 2..8");
+        MC_REQUIRE(count >= 0, "count must be >= 0");
+        if (count == 0) return;
+        cudaStream_t s = (cudaStream_t)stream;
+        Arena scratch(true);
+        scratch.alloc = g->arena.alloc;
+        scratch.stream = s;
+        run_stars(g, h, seed, first_index, count, nodes, centres, classes, nullptr, scratch, s);
+    });
+}
+
 extern "C" mc_status mc_sample(const mc_tables *t, int h, int32_t unrooted_shape, uint64_t seed,
                                uint64_t first_index, int64_t count, uint32_t *nodes, uint32_t *roots,
                                int32_t *shapes, int32_t *classes, void *stream)
 {
     return mc_sample_range(t, h, unrooted_shape, 0, 0, seed, first_index, count, nodes, roots, shapes, classes,
                            stream);
+}
+
+// Round-skipped level k: sigma'_i = sum_j sigma_ij a_j (the counted
+// spanning trees of H_i, each weighted by its rooted copies in the table)
+// and sigma*_i (the spanning stars of H_i).
+static void skip_sigmas(const mc_tables *t, const ClassCatalog *cc, int h, std::vector<int64_t> &sp,
+                        std::vector<int64_t> &ss)
+{
+    const int ncls = (int)cc->codes.size(), nu = shape_catalog().n_unrooted[h];
+    sp.assign((size_t)ncls, 0);
+    ss.assign((size_t)ncls, 0);
+    for (int i = 0; i < ncls; ++i)
+        for (int j = 0; j < nu; ++j) {
+            const int64_t sij = cc->sigma_ij[(size_t)i * nu + j];
+            sp[(size_t)i] += sij * t->copies_k[j];
+            if (t->copies_k[j] == 0) ss[(size_t)i] += sij;
+        }
+}
+
+// The graphlets only stars span (sigma'_i = 0), from star_samples
+// uncoloured stars: g_i = (S * hits*_i) / (sigma*_i * star_samples), their
+// hits the star hits; 0 without stars or star samples.
+static void star_estimates(const mc_tables *t, int h, const mc_estimate_params *p, const std::vector<int64_t> &sp,
+                           const std::vector<int64_t> &ss, double *est, uint64_t *hits, Arena &scratch,
+                           cudaStream_t s)
+{
+    const int ncls = (int)sp.size();
+    std::vector<unsigned long long> sh((size_t)ncls, 0);
+    const u128 S = ensure_star_index(t->g, h, s);
+    if (S > 0 && p->star_samples > 0) {
+        unsigned long long *dh = scratch.get<unsigned long long>((size_t)ncls);
+        MC_CUDA(cudaMemsetAsync(dh, 0, (size_t)ncls * 8, s));
+        run_stars(t->g, h, p->seed, p->first_index, p->star_samples, nullptr, nullptr, nullptr, dh, scratch, s);
+        MC_CUDA(cudaMemcpyAsync(sh.data(), dh, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+    }
+    const double Sd = (double)S;
+    for (int i = 0; i < ncls; ++i) {
+        if (sp[(size_t)i] != 0) continue;
+        hits[i] = sh[(size_t)i];
+        est[i] = (S > 0 && p->star_samples > 0 && ss[(size_t)i] > 0)
+                     ? (Sd * (double)sh[(size_t)i]) / ((double)ss[(size_t)i] * (double)p->star_samples)
+                     : 0.0;
+    }
 }
 
 extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *p, double *est,
@@ -1065,6 +1318,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         MC_REQUIRE(t && p && est && hits, "NULL argument");
         const int h = p->h;
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         MC_REQUIRE(p->samples >= 0, "samples must be >= 0");
         MC_REQUIRE(p->mode == MC_EST_UNIFORM || p->mode == MC_EST_AGS, "unknown mode");
         cudaStream_t s = (cudaStream_t)stream;
@@ -1078,13 +1332,24 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         MC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
         mc_estimate_stats st{};
         const double ip = inv_colourful_prob(t->k, h);
+        // round-skipped level k: sigma' replaces sigma, R replaces t, and the
+        // graphlets only stars span come from uncoloured stars
+        const bool skipped = t->skip_round && h == t->k;
+        std::vector<int64_t> sig_prime, sig_star;
+        if (skipped) {
+            skip_sigmas(t, cc, h, sig_prime, sig_star);
+            MC_REQUIRE(p->star_samples >= 0, "star_samples must be >= 0");
+            MC_REQUIRE(p->star_samples == 0 || (p->node_lo <= 0 && (p->node_hi <= 0 || p->node_hi == t->g->n)),
+                       "star samples cover the whole graph: no node range with star_samples");
+        }
         if (p->mode == MC_EST_UNIFORM) {
             MC_REQUIRE(p->samples > 0, "uniform estimation needs samples > 0");
             unsigned long long *dh = scratch.get<unsigned long long>((size_t)ncls);
             int64_t *dsig = scratch.get<int64_t>((size_t)ncls);
             double *dest = scratch.get<double>((size_t)ncls);
             MC_CUDA(cudaMemsetAsync(dh, 0, (size_t)ncls * 8, s));
-            MC_CUDA(cudaMemcpyAsync(dsig, cc->sigma_i.data(), (size_t)ncls * 8, cudaMemcpyHostToDevice, s));
+            MC_CUDA(cudaMemcpyAsync(dsig, skipped ? sig_prime.data() : cc->sigma_i.data(), (size_t)ncls * 8,
+                                    cudaMemcpyHostToDevice, s));
             SampleArgs a;
             fill_sample_args(a, t, h);
             RootIndex ri = root_index(t, h, -1, scratch, err + 1, s, a.allow0, a.allow1, p->node_lo, p->node_hi);
@@ -1104,7 +1369,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             a.bytes = sample_byte_counter(scratch, s);
             launch_sampler(t, a, s);
             report_sample_bytes(a.bytes, s);
-            MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, ri.R / (u128)t->copies_div(h), p->samples, ip, dest));
+            const u128 tnum = skipped ? ri.R : ri.R / (u128)t->copies_div(h);
+            MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(dh, dsig, ncls, tnum, p->samples, ip, dest));
             std::vector<unsigned long long> hh((size_t)ncls);
             MC_CUDA(cudaMemcpyAsync(hh.data(), dh, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
             MC_CUDA(cudaMemcpyAsync(est, dest, (size_t)ncls * 8, cudaMemcpyDeviceToHost, s));
@@ -1115,6 +1381,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             for (int i = 0; i < ncls; ++i) hits[i] = hh[i];
             st.samples = p->samples;
             st.batches = 1;
+            if (skipped) star_estimates(t, h, p, sig_prime, sig_star, est, hits, scratch, s);
         } else {
             // Algorithm AGS with batched speculative sampling: a batch of
             // samples is drawn from the current treelet T_j; the host replays
@@ -1158,7 +1425,12 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     w[i] = acc;
                 }
             };
-            while (cur >= 0 && ncov < ncls && drawn < p->samples) {
+            int64_t target = ncls;  // round-skipped: the graphlets only stars span are left to the stars
+            if (skipped) {
+                target = 0;
+                for (int i = 0; i < ncls; ++i) target += sig_prime[(size_t)i] > 0;
+            }
+            while (cur >= 0 && ncov < target && drawn < p->samples) {
                 if (!ris[cur].prefix) {
                     ris[cur] = root_index(t, h, cur, scratch, err + 1, s, allows[cur].first, allows[cur].second,
                                           p->node_lo, p->node_hi);
@@ -1228,6 +1500,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             if (herr[0] || herr[1]) throw Error(MC_E_INTERNAL, "sampler consistency check failed");
             st.samples = drawn;
             st.covered = ncov;
+            if (skipped) star_estimates(t, h, p, sig_prime, sig_star, est, hits, scratch, s);
         }
         if (stats) *stats = st;
     });
@@ -1291,6 +1564,7 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
     return guarded([&] {
         MC_REQUIRE(t && est && hits, "NULL argument");
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
+        MC_REQUIRE(!(t->skip_round && h >= t->k - 1), "not available on round-skipped levels");
         MC_REQUIRE(samples > 0, "samples must be > 0");
         const ClassCatalog *cc = existing_catalogue(h);
         if (!cc)
