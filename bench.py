@@ -232,9 +232,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         col = M.color(G, k, seed, out=colbuf)
-        T = M.Tables(G, col, k, BITS, zero_root=args.zero_root)
+        T = M.Tables(G, col, k, BITS, zero_root=args.zero_root, skip_round=args.skip_round)
         e1.record(stream)
-        est, hits, _ = T.estimate(k, seed=seed, samples=samples)
+        est, hits, _ = T.estimate(k, seed=seed, samples=samples,
+                                  star_samples=samples if args.skip_round else 0)
         e2.record(stream)
         T.free()
         if record:
@@ -276,6 +277,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
     entries = n * live_entries_per_node(k)
+    if args.skip_round:  # level k-1 is never built
+        entries -= n * R_H[k - 1] * math.comb(k - 1, k - 2)
     if args.zero_root:  # level k is built at colour-0 nodes only
         n0 = int((M.color(G, k, seed0, out=colbuf) == 0).sum().item())
         entries -= (n - n0) * R_H[k]
@@ -326,8 +329,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         G2 = M.Graph(rp_pin, col_pin, trusted=True)
         col = M.color(G2, k, seed0 + 77 + i, out=colbuf)
-        T2 = M.Tables(G2, col, k, BITS)
-        est, hits, _ = T2.estimate(k, seed=seed0 + 77 + i, samples=samples)
+        T2 = M.Tables(G2, col, k, BITS, zero_root=args.zero_root, skip_round=args.skip_round)
+        est, hits, _ = T2.estimate(k, seed=seed0 + 77 + i, samples=samples,
+                                   star_samples=samples if args.skip_round else 0)
         d2h = est.nbytes + hits.nbytes
         T2.free()
         G2.free()
@@ -356,6 +360,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "data": "synthetic",
         "config": {"workload": wname, "n": n, "m": nnz // 2, "k": k, "count_bits": BITS,
                    "samples_per_step": samples, "zero_root": args.zero_root,
+                   "skip_round": args.skip_round,
+                   "star_samples_per_step": samples if args.skip_round else 0,
                    "l2": "flushed between steps (256 MiB write, "
                    "outside the per-step events)", "parallelism": f"replicas{world}"},
         "samples_per_s": samples * args.steps * world / (total_ms / 1e3),
@@ -563,9 +569,13 @@ def run_serve(args):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from
-# one ncu capture of the named kernel on the named workload; None when the
-# kernel changed since the capture.
-TRAFFIC: dict = {}
+# one ncu --set full capture of the named kernel on the named workload
+# (profiles/sample_kernel_chung_lu_1m_k5.md, profiles/gather_kernel_h3_chung_lu_1m_k5.md);
+# remove an entry when its kernel changes.
+TRAFFIC: dict = {
+    ("chung_lu_1m_k5", "sample"): 2_412_321_848,     # 1M samples, 2.083 GB read + 0.329 GB written
+    ("chung_lu_1m_k5", "gather_h3"): 804_434_176,    # 0.737 GB read + 0.067 GB written
+}
 
 
 def main():
@@ -585,6 +595,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--zero-root", action="store_true",
                     help="store level k at colour-0 nodes only (Section 3.4.1)")
+    ap.add_argument("--skip-round", action="store_true",
+                    help="round skipping: level k from balanced decompositions, level k-1 not "
+                         "built, k-stars sampled uncoloured (as many as table samples)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
