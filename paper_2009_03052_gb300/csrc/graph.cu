@@ -98,7 +98,12 @@ __global__ void degree_stats(const int64_t *row_ptr, int64_t n, u128 *nch, u128 
         nhub[v] = d > HUB_CHUNK ? 1 : 0;
         if ((unsigned long long)d > md) md = (unsigned long long)d;
     }
-    atomicMax(maxdeg, md);
+    // one atomic per warp, not per thread (a single address serialises them)
+    for (int o = 16; o >= 1; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, md, o);
+        if (x > md) md = x;
+    }
+    if ((threadIdx.x & 31) == 0 && md) atomicMax(maxdeg, md);
 }
 
 // from the inclusive prefixes of chunk and hub counts: every hub writes its

@@ -145,6 +145,8 @@ struct mc_graph {
     std::mutex star_mu;
     mc::u128 *star_prefix[mc::MAXK + 1] = {nullptr};
     mc::u128 star_total[mc::MAXK + 1] = {0};
+    uint32_t *star_bucket[mc::MAXK + 1] = {nullptr};  // bucket index of the prefix (as for roots)
+    mc::u128 star_D[mc::MAXK + 1] = {0};
 };
 
 struct mc_tables {

@@ -827,6 +827,8 @@ struct StarArgs {
     const int64_t *row_ptr;
     const uint32_t *col;
     const u128 *prefix;
+    const uint32_t *bucket;  // first node whose prefix exceeds b * D, b = 0..nb
+    u128 D;
     int64_t n;
     u128 S;
     int h;
@@ -848,13 +850,17 @@ __global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarA
         const uint64_t idx = a.first_index + (uint64_t)i;
         u128 X;
         if (!draw_below(a.seed, idx, STAR_STEP, a.S, X)) { bad = true; continue; }
-        int64_t lo = 0, hi = a.n - 1;
+        // the first node whose prefix exceeds X lies in X's bucket
+        const uint64_t bk = (uint64_t)(X / a.D);
+        int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if (a.prefix[mid] > X) hi = mid; else lo = mid + 1;
         }
         const int64_t v = lo, e0 = a.row_ptr[v];
+        if (!(a.prefix[v] > X)) { bad = true; continue; }
         const uint64_t d = (uint64_t)(a.row_ptr[v + 1] - e0);
+        if (d < (uint64_t)(h - 1)) { bad = true; continue; }
         uint64_t pos[MAXK];
         int taken = 0;
         for (int s = 0; s < h - 1; ++s) {
@@ -878,11 +884,27 @@ __global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarA
             nd[m++] = u;
         }
         if (!placed) nd[m++] = c;
-        uint32_t word = 0;
+        // centre-leaf pairs are edges; leaf-leaf pairs by binary search,
+        // four searches in flight
+        uint32_t word = 0, qa[4], qb[4];
+        int qp[4], nq = 0;
+        uint64_t rb = 0;
         for (int x = 0; x < h; ++x)
-            for (int y = x + 1; y < h; ++y)
-                if (nd[x] == c || nd[y] == c || adjacent(a.row_ptr, a.col, nd[x], nd[y]))
-                    word |= 1u << pair_pos(h, x, y);
+            for (int y = x + 1; y < h; ++y) {
+                if (nd[x] == c || nd[y] == c) { word |= 1u << pair_pos(h, x, y); continue; }
+                qa[nq] = nd[x]; qb[nq] = nd[y]; qp[nq] = pair_pos(h, x, y); ++nq;
+                if (nq == 4) {
+                    bool r4[4];
+                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                    for (int q = 0; q < nq; ++q) if (r4[q]) word |= 1u << qp[q];
+                    nq = 0;
+                }
+            }
+        if (nq) {
+            bool r4[4];
+            adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+            for (int q = 0; q < nq; ++q) if (r4[q]) word |= 1u << qp[q];
+        }
         const int cls = a.lut[word];
         if (cls == 0xffff) bad = true;
         if (a.nodes) for (int x = 0; x < h; ++x) a.nodes[i * h + x] = nd[x];
@@ -957,6 +979,7 @@ struct RootIndex {
 void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
                        cudaStream_t s);
 void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t *start, cudaStream_t s);
+int64_t bucket_count(int64_t n);
 
 // Restrict a root index to the nodes [lo, hi) (hi <= 0: all nodes).
 static void restrict_range(RootIndex &ri, int64_t n, int64_t lo, int64_t hi, cudaStream_t s)
@@ -1183,17 +1206,24 @@ static u128 ensure_star_index(const mc_graph *gc, int h, cudaStream_t s)
     int *err = scratch.get<int>(1);
     MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     u128 *p = g->arena.get<u128>((size_t)std::max<int64_t>(n, 1));
-    u128 S = 0;
+    const int64_t nb = bucket_count(n);
+    uint32_t *bk = g->arena.get<uint32_t>((size_t)nb + 1);
+    u128 *dD = scratch.get<u128>(1);
+    u128 S = 0, D = 1;
     int herr = 0;
     if (n) {
         MC_LAUNCH("star_weights", s, star_weights_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->row_ptr, n, h - 1, p, err));
         inclusive_scan_u128(p, n, err, scratch, s);
+        build_buckets(p, n, nb, dD, bk, s);
         MC_CUDA(cudaMemcpyAsync(&S, p + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(&D, dD, sizeof(u128), cudaMemcpyDeviceToHost, s));
     }
     MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
     if (herr) throw Error(MC_E_OVERFLOW, "the number of stars does not fit in 128 bits");
     g->star_total[h] = S;
+    g->star_D[h] = D;
+    g->star_bucket[h] = bk;
     g->star_prefix[h] = p;  // published last
     return S;
 }
@@ -1213,6 +1243,8 @@ static void run_stars(const mc_graph *g, int h, uint64_t seed, uint64_t first_in
     a.row_ptr = g->row_ptr;
     a.col = g->col;
     a.prefix = g->star_prefix[h];
+    a.bucket = g->star_bucket[h];
+    a.D = g->star_D[h];
     a.n = g->n;
     a.S = S;
     a.h = h;
@@ -1425,6 +1457,21 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     w[i] = acc;
                 }
             };
+            // Batch sizing only (the outcome does not depend on it): hits per
+            // class among the samples drawn with each T_j predict how many
+            // more samples T_j needs until some graphlet is covered.
+            std::vector<uint64_t> hj((size_t)nu * ncls, 0);
+            auto predict = [&](int j) -> int64_t {
+                if (nj[j] == 0) return -1;
+                double best = -1.0;
+                for (int i = 0; i < ncls; ++i) {
+                    const uint64_t c = hj[(size_t)j * ncls + i];
+                    if (covered[(size_t)i] || c == 0) continue;
+                    const double need = (double)(cbar - (int64_t)hv[(size_t)i]) * (double)nj[j] / (double)c;
+                    if (best < 0.0 || need < best) best = need;
+                }
+                return best < 0.0 ? -1 : (int64_t)best;
+            };
             int64_t target = ncls;  // round-skipped: the graphlets only stars span are left to the stars
             if (skipped) {
                 target = 0;
@@ -1465,6 +1512,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     nj[cur]++;
                     drawn++;
                     hv[(size_t)i]++;
+                    hj[(size_t)cur * ncls + i]++;
                     if ((int64_t)hv[(size_t)i] == cbar && !covered[(size_t)i]) {
                         covered[(size_t)i] = 1;
                         ncov++;
@@ -1487,7 +1535,13 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                         break;
                     }
                 }
-                B = switched ? bmin : std::min(2 * B, bmax);
+                if (p->batch > 0) {
+                    B = p->batch;
+                } else {
+                    const int64_t q = cur >= 0 ? predict(cur) : -1;
+                    if (q >= 0) B = std::min<int64_t>(std::max<int64_t>(q + q / 4 + 4096, 4096), bmax);
+                    else B = switched ? bmin : std::min(2 * B, bmax);
+                }
             }
             weights();
             for (int i = 0; i < ncls; ++i) {
