@@ -151,6 +151,26 @@ mc_status mc_build_tables_batch(int count, const mc_graph *const *graphs, const 
                                 int count_bits, uint32_t flags, const mc_allocator *alloc, void *stream,
                                 mc_tables **out, int64_t *node_offsets);
 
+/* Rebuild t in place for a new colouring (device or host uint8[n], values
+ * < k): the same graph, k, count width and flags; every buffer of the first
+ * build is reused.  The call allocates nothing, only enqueues kernels,
+ * memsets and one copy of the colours on `stream`, and never synchronises,
+ * so it can be captured into a CUDA graph and replayed (write the next
+ * colouring into the same buffer before each replay; colors == the tables'
+ * own colour buffer skips the copy).  Checks (a colour >= k, overflow) are
+ * recorded on the device and reported by the next call that reads the
+ * tables (mc_total, mc_sample, mc_estimate_counts, mc_read_table) or by
+ * mc_tables_status, which also reads the new level-k total back
+ * (synchronising `stream`); issue them on the rebuild's stream or after
+ * synchronising it.  A replay of a captured rebuild runs no host code: call
+ * mc_tables_status after each replay before any other call on t.  mc_estimate_uniform_noalloc after a rebuild needs
+ * mc_tables_status first.  Root indices of levels below k made by earlier
+ * calls are rebuilt on first use.  No other call may use t while a rebuild
+ * is in flight.  The paper has no counterpart: it builds once per
+ * colouring. */
+mc_status mc_rebuild_tables(mc_tables *t, const uint8_t *colors, void *stream);
+mc_status mc_tables_status(const mc_tables *t, void *stream);
+
 /* Layout of the level-h table (which = 0: counts c, h = 1..k; which = 1:
  * neighbour sums S, h = 1..k-1).  Row v holds row_entries entries of
  * entry_bytes (8 or 16, little-endian, low word first).  Entry

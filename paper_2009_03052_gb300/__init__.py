@@ -38,7 +38,8 @@ EXPORTED = [
     "mc_class_codes", "mc_sigma", "mc_last_error", "mc_profile_enable", "mc_profile_reset",
     "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
-    "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars",
+    "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars", "mc_rebuild_tables",
+    "mc_tables_status",
 ]
 
 
@@ -123,6 +124,8 @@ def load(path: str | None = None):
         lib.mc_server_free.argtypes = [P]
         lib.mc_server_free.restype = None
         lib.mc_star_total.argtypes = [P, C.c_int, P, P]
+        lib.mc_rebuild_tables.argtypes = [P, P, P]
+        lib.mc_tables_status.argtypes = [P, P]
         lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
         _lib = lib
         return lib
@@ -295,6 +298,17 @@ class Tables:
                                       None if own_memory else C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
+
+    def rebuild(self, colors, stream=None):
+        """mc_rebuild_tables: the whole build again for a new colouring (device
+        uint8 tensor), in place, without allocating or synchronising -- it
+        can be captured into a CUDA graph."""
+        _check(load().mc_rebuild_tables(self.handle, _ptr(colors) if self.graph.n else None,
+                                        _stream_ptr(stream)))
+
+    def status(self, stream=None):
+        """mc_tables_status: checks of the last rebuild (synchronises)."""
+        _check(load().mc_tables_status(self.handle, _stream_ptr(stream)))
 
     @classmethod
     def batch(cls, graphs, colors, k: int, count_bits: int = 64, zero_root: bool = False,

@@ -551,11 +551,17 @@ void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t
 
 int64_t bucket_count(int64_t n) { return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)1 << 22)); }
 
-__global__ void check_colours_kernel(const uint8_t *colors, int64_t n, int k, int *err)
+// A colour >= k is reported and replaced by 0 in the tables' own copy, so
+// the kernels after this one never index past a colour's slot; the build
+// then fails when its error flags are read.
+__global__ void check_colours_kernel(uint8_t *colors, int64_t n, int k, int *err)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        if (colors[v] >= k) atomicOr(err, ERR_COLOUR);
+        if (colors[v] >= k) {
+            atomicOr(err, ERR_COLOUR);
+            colors[v] = 0;
+        }
 }
 
 __global__ void fill_ones_kernel(void *dst, int64_t n, int bytes)
@@ -570,14 +576,22 @@ __global__ void fill_ones_kernel(void *dst, int64_t n, int bytes)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s)
+static int64_t scan_tiles(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+// the scan with a caller-provided tile-sum buffer of scan_tiles(n) entries
+static void inclusive_scan_u128_buf(u128 *x, int64_t n, int *err, u128 *ts, cudaStream_t s)
 {
     if (n <= 0) return;
-    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    u128 *ts = scratch.get<u128>((size_t)ntiles);
+    const int64_t ntiles = scan_tiles(n);
     MC_LAUNCH("scan_tiles", s, scan_tiles_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(x, n, ts, err));
     MC_LAUNCH("scan_tile_sums", s, scan_tile_sums_kernel<<<1, 1024, 0, s>>>(ts, ntiles, err));
     MC_LAUNCH("scan_apply", s, scan_apply_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(x, n, ts));
+}
+
+void inclusive_scan_u128(u128 *x, int64_t n, int *err, Arena &scratch, cudaStream_t s)
+{
+    if (n <= 0) return;
+    inclusive_scan_u128_buf(x, n, err, scratch.get<u128>((size_t)scan_tiles(n)), s);
 }
 
 ExactDiv make_div(int beta)
@@ -652,7 +666,7 @@ template <typename CT> static void launch_gather(const GatherArgs &ga, int G, in
     }
 }
 
-template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &scratch, cudaStream_t s)
+template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStream_t s)
 {
     const mc_graph *g = t->g;
     const Geometry &G = t->geo;
@@ -665,7 +679,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
                                       g->row_ptr, g->col, t->ecol, t->colors, n, k, t->scol, t->coff,
                                       (CT *)t->S[1]));
     if (g->n_hubs) {
-        uint32_t *ccnt = scratch.get<uint32_t>((size_t)g->n_chunks * k);
+        uint32_t *ccnt = t->ccnt;
         MC_LAUNCH("colour_blocks_hub", s, hub_chunk_counts_kernel<<<grid_for(g->n_chunks * 32, 256), 256, 0, s>>>(
                                               t->ecol, g->chunk_e0, g->chunk_e1, g->n_chunks, k, ccnt));
         MC_LAUNCH("colour_blocks_hub", s, hub_chunk_prefix_kernel<CT><<<grid_for(g->n_hubs * 32, 256), 256, 0, s>>>(
@@ -731,6 +745,56 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, Arena &s
 
 using namespace mc;
 
+// Every launch of a build for the colours in `colors`, on stream s, into the
+// buffers of t: no allocation, no host read, no synchronisation (so a
+// rebuild can be captured into a CUDA graph).
+static void enqueue_build(mc_tables *t, const uint8_t *colors, cudaStream_t s)
+{
+    const mc_graph *g = t->g;
+    const int64_t n = g->n;
+    const int k = t->k;
+    int *err = t->dev_err;
+    MC_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+    if (n) {
+        // the tables' own copy of the colours, checked before any kernel reads them
+        if (colors != t->colors)
+            MC_CUDA(cudaMemcpyAsync(t->colors, colors, (size_t)n, cudaMemcpyDefault, s));
+        MC_LAUNCH("check_colours", s, check_colours_kernel<<<grid_for(n, 256), 256, 0, s>>>(t->colors, n, k, err));
+    }
+    if (g->nnz)
+        MC_LAUNCH("edge_colours", s, edge_colours_kernel<<<grid_for(g->nnz, 256), 256, 0, s>>>(
+                                         g->col, t->colors, g->nnz, t->ecol));
+    if (t->bits == 64) build_levels<uint64_t>(t, err, s);
+    else build_levels<u128>(t, err, s);
+    // root index of the top level (the level sampled by default); the other
+    // levels get theirs on first use
+    if (n) {
+        launch_row_totals(t, k, ~0ull, ~0ull, t->prefix[k], err, s);
+        inclusive_scan_u128_buf(t->prefix[k], n, err, t->scan_tmp, s);
+        build_buckets(t->prefix[k], n, t->nbucket, t->dev_D, t->bucket[k], s);
+    }
+}
+
+// Read the level-k total, the bucket width and the error flags back.
+static void finish_build(mc_tables *t, cudaStream_t s)
+{
+    const int64_t n = t->g->n;
+    int herr = 0;
+    u128 R = 0, D = 1;
+    MC_CUDA(cudaMemcpyAsync(&herr, t->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (n) {
+        MC_CUDA(cudaMemcpyAsync(&R, t->prefix[t->k] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaMemcpyAsync(&D, t->dev_D, sizeof(u128), cudaMemcpyDeviceToHost, s));
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    if (herr & ERR_COLOUR) throw Error(MC_E_INVALID, "a colour is >= k");
+    if (herr & ERR_OVERFLOW)
+        throw Error(MC_E_OVERFLOW, "a count does not fit in " + std::to_string(t->bits) + " bits");
+    if (herr & ERR_INEXACT) throw Error(MC_E_INTERNAL, "a merge numerator is not divisible by beta");
+    t->R[t->k] = R;
+    t->bucketD[t->k] = D;
+}
+
 extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
                                      uint32_t flags, const mc_allocator *alloc, void *stream,
                                      mc_tables **out)
@@ -757,27 +821,18 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         t->geo = make_geometry(k);
         t->arena.stream = s;
         if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
-        Arena scratch(true);
-        scratch.alloc = t->arena.alloc;
-        scratch.stream = s;
         const int64_t n = g->n;
         const Geometry &G = t->geo;
         const size_t cb = count_bits / 8;
-        int *err = scratch.get<int>(4);
-        MC_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+        // every buffer a build writes, kept for rebuilds
+        t->dev_err = t->arena.get<int>(4);
+        t->dev_D = t->arena.get<u128>(1);
+        t->scan_tmp = t->arena.get<u128>((size_t)std::max<int64_t>(scan_tiles(n), 1));
+        if (g->n_hubs) t->ccnt = t->arena.get<uint32_t>((size_t)g->n_chunks * k);
         t->colors = t->arena.get<uint8_t>((size_t)n);
-        if (n) {
-            MC_CUDA(cudaMemcpyAsync(t->colors, colors, (size_t)n, cudaMemcpyDefault, s));
-            MC_LAUNCH("check_colours", s, check_colours_kernel<<<grid_for(n, 256), 256, 0, s>>>(t->colors, n, k, err));
-        }
         t->ecol = t->arena.get<uint8_t>((size_t)g->nnz);
         t->scol = t->arena.get<uint32_t>((size_t)g->nnz);
         t->coff = t->arena.get<int32_t>((size_t)n * (k + 1));
-        if (g->nnz) {
-            MC_LAUNCH("edge_colours", s, edge_colours_kernel<<<grid_for(g->nnz, 256), 256, 0, s>>>(
-                                             g->col, t->colors, g->nnz, t->ecol));
-
-        }
         // programs
         const Programs &P = programs(k, t->skip_round);
         for (int j = 0; j < 32; ++j) t->copies_k[j] = P.copies[j];
@@ -804,41 +859,65 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
             if (!t->level_missing(h)) t->S[h] = t->arena.get<uint8_t>((size_t)n * G.Ws[h] * cb);
         for (int h = 2; h <= k - 1; ++h)
             if (!t->level_missing(h)) t->Sp[h] = t->arena.get<uint8_t>((size_t)g->n_chunks * G.Ws[h] * cb);
-
-        if (count_bits == 64) build_levels<uint64_t>(t, err, scratch, s);
-        else build_levels<u128>(t, err, scratch, s);
-        // node prefixes of the level totals, for the root draw
-        // root index of the top level (the level sampled by default); the
-        // other levels get theirs on first use
         t->nbucket = bucket_count(n);
-        u128 *dD = scratch.get<u128>(1);
         t->prefix[k] = t->arena.get<u128>((size_t)n);
         t->bucket[k] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
-        launch_row_totals(t, k, ~0ull, ~0ull, t->prefix[k], err, s);
-        inclusive_scan_u128(t->prefix[k], n, err, scratch, s);
-        build_buckets(t->prefix[k], n, t->nbucket, dD, t->bucket[k], s);
-        int herr = 0;
-        MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if (n) {
-            MC_CUDA(cudaMemcpyAsync(&t->R[k], t->prefix[k] + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
-            MC_CUDA(cudaMemcpyAsync(&t->bucketD[k], dD, sizeof(u128), cudaMemcpyDeviceToHost, s));
-        }
-        MC_CUDA(cudaStreamSynchronize(s));
-        if (herr & ERR_COLOUR) throw Error(MC_E_INVALID, "a colour is >= k");
-        if (herr & ERR_OVERFLOW)
-            throw Error(MC_E_OVERFLOW, "a count does not fit in " + std::to_string(count_bits) + " bits");
-        if (herr & ERR_INEXACT) throw Error(MC_E_INTERNAL, "a merge numerator is not divisible by beta");
+        enqueue_build(t, colors, s);
+        finish_build(t, s);
     });
     if (st != MC_OK) { delete t; return st; }
     *out = t;
     return MC_OK;
 }
 
-void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
+extern "C" mc_status mc_rebuild_tables(mc_tables *t, const uint8_t *colors, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t, "tables is NULL");
+        MC_REQUIRE(colors || t->g->n == 0, "colors is NULL");
+        std::lock_guard<std::mutex> lock(t->idx_mu);
+        enqueue_build(t, colors, (cudaStream_t)stream);
+        t->stale = true;
+        t->broken.clear();
+        for (int h = 2; h < t->k; ++h) t->level_stale[h] = t->prefix[h] != nullptr;
+    });
+}
+
+void mc::refresh_tables(const mc_tables *tc, cudaStream_t s, bool force)
 {
     mc_tables *t = const_cast<mc_tables *>(tc);
     std::lock_guard<std::mutex> lock(t->idx_mu);
-    if (t->prefix[h] || h < 2) return;
+    if (force) {
+        // a replayed capture runs no host code: treat the device state as new
+        t->stale = true;
+        t->broken.clear();
+        for (int h = 2; h < t->k; ++h) t->level_stale[h] = t->prefix[h] != nullptr;
+    }
+    if (!t->broken.empty()) throw Error(MC_E_INVALID, "the last rebuild failed: " + t->broken);
+    if (!t->stale) return;
+    try {
+        finish_build(t, s);
+    } catch (const Error &e) {
+        t->broken = e.what();
+        throw;
+    }
+    t->stale = false;
+}
+
+extern "C" mc_status mc_tables_status(const mc_tables *t, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t, "tables is NULL");
+        refresh_tables(t, (cudaStream_t)stream, true);
+    });
+}
+
+void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
+{
+    mc_tables *t = const_cast<mc_tables *>(tc);
+    refresh_tables(t, s);
+    std::lock_guard<std::mutex> lock(t->idx_mu);
+    if (h < 2 || (t->prefix[h] && !t->level_stale[h])) return;
     if (t->level_missing(h)) throw Error(MC_E_INVALID, "level h was skipped (round skipping)");
     const int64_t n = t->g->n;
     Arena scratch(true);
@@ -847,8 +926,9 @@ void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
     int *err = scratch.get<int>(1);
     u128 *dD = scratch.get<u128>(1);
     MC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    u128 *p = t->arena.get<u128>((size_t)n);
-    uint32_t *bk = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
+    // a stale index (from an older colouring) is rebuilt in its own buffers
+    u128 *p = t->prefix[h] ? t->prefix[h] : t->arena.get<u128>((size_t)n);
+    uint32_t *bk = t->bucket[h] ? t->bucket[h] : t->arena.get<uint32_t>((size_t)t->nbucket + 1);
     launch_row_totals(t, h, ~0ull, ~0ull, p, err, s);
     inclusive_scan_u128(p, n, err, scratch, s);
     build_buckets(p, n, t->nbucket, dD, bk, s);
@@ -865,6 +945,7 @@ void mc::ensure_level_index(const mc_tables *tc, int h, cudaStream_t s)
     t->bucketD[h] = D;
     t->bucket[h] = bk;
     t->prefix[h] = p;  // published last
+    t->level_stale[h] = false;
 }
 
 extern "C" void mc_free_tables(mc_tables *t)
@@ -936,6 +1017,7 @@ extern "C" mc_status mc_total_range(const mc_tables *t, int h, int32_t unrooted_
 {
     return guarded([&] {
         MC_REQUIRE(t && rooted && unrooted_count, "NULL argument");
+        refresh_tables(t, (cudaStream_t)stream);
         MC_REQUIRE(h >= 1 && h <= t->k, "h must be in 1..k");
         MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         const ShapeCatalog &cat = shape_catalog();
@@ -1054,6 +1136,7 @@ extern "C" mc_status mc_read_table(const mc_tables *t, int h, int which, void *d
 {
     return guarded([&] {
         MC_REQUIRE(t && dst, "NULL argument");
+        refresh_tables(t, (cudaStream_t)stream);
         MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
         MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
         MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");

@@ -119,6 +119,10 @@ void prof_end(ProfSpan &span, cudaStream_t s);
 // Make sure level h's root index (node prefix of the level totals, R and
 // the root-search buckets) exists; builds and publishes it on first use.
 void ensure_level_index(const mc_tables *t, int h, cudaStream_t s);
+// After mc_rebuild_tables: read the new level-k total and bucket width and
+// the error flags back (synchronises s); throws if the rebuild failed.
+// force: re-read even without a rebuild through the API (a replayed graph).
+void refresh_tables(const mc_tables *t, cudaStream_t s, bool force = false);
 
 // Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
@@ -182,5 +186,14 @@ struct mc_tables {
     int32_t *m_off[mc::MAXK + 1] = {nullptr};
     uint32_t *m_terms[mc::MAXK + 1] = {nullptr};
     int16_t *g_map[mc::MAXK + 1] = {nullptr};
+    // kept for in-place rebuilds (mc_rebuild_tables): error flags, hub colour
+    // counts, scan tile sums and the bucket width of level k, all on the device
+    int *dev_err = nullptr;
+    uint32_t *ccnt = nullptr;
+    mc::u128 *scan_tmp = nullptr;
+    mc::u128 *dev_D = nullptr;
+    bool stale = false;                         // rebuilt since R[k], bucketD[k] were read back
+    bool level_stale[mc::MAXK + 1] = {false};   // root index of level h from an older colouring
+    std::string broken;                         // set when a rebuild failed its checks
     mc::Arena arena;
 };

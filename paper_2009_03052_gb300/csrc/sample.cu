@@ -841,6 +841,9 @@ struct StarArgs {
     int *err;
 };
 
+// V: the type of the centre draw (64 bits when S < 2^64, the same value as
+// the 128-bit draw)
+template <typename V>
 __global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarArgs a)
 {
     bool bad = false;
@@ -848,17 +851,17 @@ __global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarA
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.count;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t idx = a.first_index + (uint64_t)i;
-        u128 X;
-        if (!draw_below(a.seed, idx, STAR_STEP, a.S, X)) { bad = true; continue; }
+        V X;
+        if (!draw_below(a.seed, idx, STAR_STEP, (V)a.S, X)) { bad = true; continue; }
         // the first node whose prefix exceeds X lies in X's bucket
-        const uint64_t bk = (uint64_t)(X / a.D);
+        const uint64_t bk = (uint64_t)(X / (V)a.D);
         int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (a.prefix[mid] > X) hi = mid; else lo = mid + 1;
+            if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
         }
         const int64_t v = lo, e0 = a.row_ptr[v];
-        if (!(a.prefix[v] > X)) { bad = true; continue; }
+        if (!(a.prefix[v] > (u128)X)) { bad = true; continue; }
         const uint64_t d = (uint64_t)(a.row_ptr[v + 1] - e0);
         if (d < (uint64_t)(h - 1)) { bad = true; continue; }
         uint64_t pos[MAXK];
@@ -1154,6 +1157,7 @@ extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
         MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         MC_REQUIRE(count >= 0, "count must be >= 0");
+        refresh_tables(t, (cudaStream_t)stream);
         MC_REQUIRE(unrooted_shape < shape_catalog().n_unrooted[h], "unrooted shape out of range");
         if (count == 0) return;
         cudaStream_t s = (cudaStream_t)stream;
@@ -1257,7 +1261,10 @@ static void run_stars(const mc_graph *g, int h, uint64_t seed, uint64_t first_in
     a.classes = classes;
     a.hist = hist;
     a.err = err;
-    MC_LAUNCH("star_sample", s, star_kernel<<<grid_for(count, 256), 256, 0, s>>>(a));
+    if ((S >> 64) == 0)
+        MC_LAUNCH("star_sample", s, star_kernel<uint64_t><<<grid_for(count, 256), 256, 0, s>>>(a));
+    else
+        MC_LAUNCH("star_sample", s, star_kernel<u128><<<grid_for(count, 256), 256, 0, s>>>(a));
     int herr = 0;
     MC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
@@ -1352,6 +1359,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
         MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
         MC_REQUIRE(p->samples >= 0, "samples must be >= 0");
+        refresh_tables(t, (cudaStream_t)stream);
         MC_REQUIRE(p->mode == MC_EST_UNIFORM || p->mode == MC_EST_AGS, "unknown mode");
         cudaStream_t s = (cudaStream_t)stream;
         const ClassCatalog *cc = class_catalog_sigma(h);
@@ -1620,6 +1628,8 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
         MC_REQUIRE(!(t->skip_round && h >= t->k - 1), "not available on round-skipped levels");
         MC_REQUIRE(samples > 0, "samples must be > 0");
+        MC_REQUIRE(!t->stale && t->broken.empty(),
+                   "tables rebuilt since their totals were read: call mc_tables_status first");
         const ClassCatalog *cc = existing_catalogue(h);
         if (!cc)
             throw Error(MC_E_INVALID, "the graphlet catalogue of this size does not exist on this device yet "
