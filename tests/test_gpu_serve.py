@@ -103,3 +103,45 @@ def test_tiny_budget_queues_requests_with_the_same_results(setup):
         _check(r, x, w)
     assert max(x["queue_us"] for x in res) > 0
     S.free()
+
+
+@pytest.mark.slow
+def test_serving_workload_full_size(oracle):
+    # Chung-Lu n = 2M, m ~ 20M, k = 8, 128-bit counts: star totals by their
+    # closed form at every level; samples of sizes 5..8 drawn through the
+    # server are the same as drawn directly, and each is colourful,
+    # connected and carries the oracle's class of its induced subgraph
+    import torch
+    import paper_2009_03052_gb300 as M
+    from oracle import catalog as cat
+    from tests import brute
+    k = 8
+    g = synth.chung_lu(2_000_000, 20_000_000, 2.5, max_degree=10_000.0, seed=0)
+    G = M.Graph.from_csr(g, trusted=True)
+    col = M.color(G, k, 1)
+    colors = col.cpu().numpy()
+    T = M.Tables(G, col, k, 128, own_memory=True)
+    stars = brute.star_totals(g, colors, k)
+    assert T.total(2)[1] == stars[2]
+    for h in range(3, k + 1):
+        assert T.total(h, cat.unrooted_id("10" * (h - 1)))[1] == stars[h], h
+    S = M.Server([T], slots=4)
+    ids = [(h, S.submit_sample(0, h, 50 + h, 500)) for h in (5, 6, 7, 8)]
+    for h, rid in ids:
+        res = S.wait(rid)
+        nodes, _, _, cls = T.sample(h, 50 + h, 0, 500, roots=False, shapes=False)
+        nodes = nodes.cpu().numpy().astype(np.uint32)
+        assert np.array_equal(res["nodes"], nodes) and np.array_equal(res["classes"], cls.cpu().numpy())
+        for s in range(0, 500, 5):
+            vs = nodes[s].astype(np.int64)
+            assert len(set(colors[vs].tolist())) == h
+            w = 0
+            for a in range(h):
+                row = g.col[g.row_ptr[vs[a]]:g.row_ptr[vs[a] + 1]]
+                for b in range(a + 1, h):
+                    i = np.searchsorted(row, vs[b])
+                    w = (w << 1) | int(i < len(row) and row[i] == vs[b])
+            assert res["classes"][s] == oracle.class_of_word(h, w) >= 0
+    S.free()
+    T.free()
+    torch.cuda.synchronize()
