@@ -92,9 +92,13 @@ def _load():
         lib.oc_sigma_matrix.argtypes = [C.c_int, C.c_int, i32p, i32p, i32p, i32p, i32p, i32p,
                                         i32p, C.c_int, i64p, C.c_int]
         lib.oc_estimate_uniform.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64,
-                                            i64p, C.c_int64, i64p, f64p, u64p]
+                                            i64p, C.c_int64, i64p, C.c_uint32, f64p, u64p]
         lib.oc_estimate_ags.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
-                                        i64p, C.c_int, C.c_int64, i64p, i64p, f64p, u64p, i64p]
+                                        i64p, C.c_int, C.c_int64, i64p, i64p, C.c_uint32, f64p, u64p,
+                                        i64p]
+        lib.oc_color_biased.argtypes = [C.c_int64, C.c_int, C.c_uint64, C.c_uint32, u8p]
+        lib.oc_inv_colorful_prob.restype = C.c_double
+        lib.oc_inv_colorful_prob.argtypes = [C.c_int, C.c_int, C.c_uint32]
         lib.oc_star_total.argtypes = [P, C.c_int, u64p]
         lib.oc_sample_stars.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64,
                                         u32p, u32p, i32p]
@@ -136,6 +140,18 @@ def color(n: int, k: int, seed: int) -> np.ndarray:
     out = np.zeros(max(n, 1), np.uint8)
     _load().oc_color(n, k, seed, out)
     return out[:n]
+
+
+def color_biased(n: int, k: int, seed: int, bias_q32: int) -> np.ndarray:
+    """Biased colouring (Section 3.4.3): colours 1..k-1 with probability
+    lambda = bias_q32 / 2^32 each, colour 0 otherwise."""
+    out = np.zeros(max(n, 1), np.uint8)
+    _check(_load().oc_color_biased(n, k, seed, bias_q32, out))
+    return out[:n]
+
+
+def inv_colorful_prob_biased(k: int, h: int, bias_q32: int) -> float:
+    return float(_load().oc_inv_colorful_prob(k, h, bias_q32))
 
 
 # ---------------------------------------------------------------------------
@@ -296,16 +312,16 @@ class Tables:
         return (np.ascontiguousarray(s_ij @ a), np.ascontiguousarray(s_ij[:, star]))
 
     def estimate_uniform(self, h: int, seed: int, n_samples: int, first_index: int = 0,
-                         star_samples: int = 0):
+                         star_samples: int = 0, bias_q32: int = 0):
         s_use, s_star = self._skip_sigmas(h)
         est = np.zeros(len(s_use), np.float64)
         hits = np.zeros(len(s_use), np.uint64)
         _check(_load().oc_estimate_uniform(self._h, h, seed, first_index, n_samples,
-                                           s_use, star_samples, s_star, est, hits))
+                                           s_use, star_samples, s_star, bias_q32, est, hits))
         return est, hits
 
     def estimate_ags(self, h: int, seed: int, max_samples: int, cbar: int = 1000,
-                     first_index: int = 0, star_samples: int = 0):
+                     first_index: int = 0, star_samples: int = 0, bias_q32: int = 0):
         _, s_ij = sigma(h)
         s_prime, s_star = self._skip_sigmas(h)
         est = np.zeros(s_ij.shape[0], np.float64)
@@ -313,7 +329,7 @@ class Tables:
         stats = np.zeros(3, np.int64)
         _check(_load().oc_estimate_ags(self._h, h, seed, first_index, max_samples, cbar,
                                        np.ascontiguousarray(s_ij), s_ij.shape[1], star_samples,
-                                       s_prime, s_star, est, hits, stats))
+                                       s_prime, s_star, bias_q32, est, hits, stats))
         return est, hits, {"samples": int(stats[0]), "switches": int(stats[1]),
                            "covered": int(stats[2])}
 

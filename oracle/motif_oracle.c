@@ -62,6 +62,24 @@ void oc_color(int64_t n, int k, uint64_t seed, uint8_t *colors)
     }
 }
 
+/* Biased colouring (Section 3.4.3): colours 1..k-1 each with probability
+ * lambda = L / 2^32, colour 0 with 1 - (k-1) lambda; (k-1) L <= 2^32.  The
+ * same counter as above; x = x0: colour 1 + floor(x / L) when x < (k-1) L,
+ * else 0.  L = 0 is the uniform colouring above. */
+int oc_color_biased(int64_t n, int k, uint64_t seed, uint32_t L, uint8_t *colors)
+{
+    if (L == 0) { oc_color(n, k, seed, colors); return OC_OK; }
+    if ((uint64_t)(k - 1) * L > 4294967296ull) return OC_INVALID;
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    const uint64_t rare = (uint64_t)(k - 1) * L;
+    for (int64_t v = 0; v < n; ++v) {
+        uint32_t ctr[4] = { (uint32_t)v, 0u, 0u, 0xC010u }, x[4];
+        oc_philox4x32_10(ctr, key, x);
+        colors[v] = (uint8_t)((uint64_t)x[0] < rare ? 1u + x[0] / L : 0u);
+    }
+    return OC_OK;
+}
+
 /* uniform(W), W >= 1: 128 bits from Philox with counter
  * (index_lo, index_hi, step, attempt), masked to the smallest power of two
  * >= W, accepted when < W, else attempt + 1. */
@@ -937,6 +955,26 @@ static double inv_colorful_prob(int k, int h)
     return num / den;
 }
 
+/* 1 / p under the biased colouring: an h-node set is colourful when its
+ * colours are distinct, with probability h! e_h(p_0, lambda, ..., lambda) =
+ * h! (C(k-1,h) lambda^h + C(k-1,h-1) lambda^(h-1) p_0), p_0 = 1 - (k-1) lambda
+ * (Section 3.4.3 gives the leading terms j! lambda^j and j! lambda^(j-1)).
+ * lambda and p_0 are exact doubles; the rest is evaluated in this order. */
+static double inv_colorful_prob_biased(int k, int h, uint32_t L)
+{
+    if (L == 0) return inv_colorful_prob(k, h);
+    const double lam = (double)L / 4294967296.0;
+    const double p0 = (double)(4294967296ull - (uint64_t)(k - 1) * L) / 4294967296.0;
+    double lh1 = 1.0;
+    for (int i = 0; i < h - 1; ++i) lh1 *= lam;
+    double fact = 1.0;
+    for (int i = 2; i <= h; ++i) fact *= (double)i;
+    const double p = fact * ((double)binom(k - 1, h) * (lh1 * lam) + (double)binom(k - 1, h - 1) * (lh1 * p0));
+    return 1.0 / p;
+}
+
+double oc_inv_colorful_prob(int k, int h, uint32_t L) { return inv_colorful_prob_biased(k, h, L); }
+
 static double u128_to_double(u128 x) { return (double)x; }
 
 /* Graphlets that only stars span (sigma'_i = 0) on a round-skipped level k
@@ -987,7 +1025,7 @@ static int star_estimates(const oc_tables *t, int h, uint64_t seed, uint64_t fir
  * the graphlets with sigma'_i = 0 get 0 here and their estimate from
  * n_star uncoloured stars (star_estimates). */
 int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t N,
-                        const int64_t *sigma, int64_t n_star, const int64_t *sigma_star,
+                        const int64_t *sigma, int64_t n_star, const int64_t *sigma_star, uint32_t bias,
                         double *est, uint64_t *hits)
 {
     if (h < 2 || level_missing(t, h) || N <= 0) return OC_INVALID;
@@ -1013,7 +1051,7 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
         hits[cls]++;
     }
     free(ri.prefix);
-    const double td = u128_to_double(tot), ip = inv_colorful_prob(t->k, h);
+    const double td = u128_to_double(tot), ip = inv_colorful_prob_biased(t->k, h, bias);
     for (int i = 0; i < ncls; ++i)
         est[i] = sigma[i] > 0 ? ((td * (double)hits[i]) / ((double)sigma[i] * (double)N)) * ip : 0.0;
     if (skipped) return star_estimates(t, h, seed, first_index, n_star, sigma, sigma_star, est, hits);
@@ -1044,7 +1082,7 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
  * stats: [0] samples drawn, [1] switches, [2] graphlets covered. */
 int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t max_samples,
                     int64_t cbar, const int64_t *sigma_ij, int n_unrooted, int64_t n_star,
-                    const int64_t *sigma_prime, const int64_t *sigma_star,
+                    const int64_t *sigma_prime, const int64_t *sigma_star, uint32_t bias,
                     double *est, uint64_t *hits, int64_t *stats)
 {
     if (h < 2 || level_missing(t, h) || max_samples < 0 || cbar < 1) return OC_INVALID;
@@ -1118,7 +1156,7 @@ finish:
         w[a] = acc;
     }
     {
-        const double ip = inv_colorful_prob(t->k, h);
+        const double ip = inv_colorful_prob_biased(t->k, h, bias);
         for (int a = 0; a < ncls; ++a) est[a] = w[a] > 0.0 ? ((double)hits[a] / w[a]) * ip : 0.0;
     }
     stats[0] = drawn; stats[1] = switches; stats[2] = ncov;
