@@ -318,6 +318,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     build_kernels = [nm for nm in prof if nm.startswith(("gather", "merge"))]
     roof_build = roofline(max(build_kernels, key=lambda x: prof[x][0])) if build_kernels else None
 
+    # non-zero entries of one build (what a zero-suppressed table keeps),
+    # counted outside the timed steps
+    Tn = M.Tables(G, M.color(G, k, seed0, out=colbuf), k, BITS, zero_root=args.zero_root,
+                  skip_round=args.skip_round)
+    nonzero = sum(Tn.nonzeros(h) for h in range(1, k + 1) if not (args.skip_round and h == k - 1))
+    Tn.free()
+
     # end to end through the C ABI with host buffers: graph upload, colour,
     # build, sample, estimates copied back
     e2e_ms = []
@@ -368,6 +375,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "samples_per_s": samples * args.steps * world / (total_ms / 1e3),
         "phases_ms": {"build": round(build_ms, 3), "sample_classify_estimate": round(sample_ms, 3)},
         "build_entries_per_s": entries / (build_ms / 1e3),
+        "nonzero_entries": int(nonzero), "nonzero_entries_per_s": nonzero / (build_ms / 1e3),
         "roofline": roof, "roofline_build": roof_build, "top_kernel": top, "kernels": kernels,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),

@@ -86,6 +86,15 @@ mc_status mc_graph_info(const mc_graph *g, int64_t *n, int64_t *nnz, int64_t *ma
  * first word of Philox4x32-10 (Salmon et al., SC 2011) at key = seed
  * (low word first) and counter = (v, 0, 0, 0xC010). */
 mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, void *stream);
+/* Biased colouring (Section 3.4.3): colours 1..k-1 each with probability
+ * lambda = lambda_q32 / 2^32, colour 0 with 1 - (k-1) lambda ((k-1) lambda
+ * <= 1, else MC_E_INVALID).  Same counter and key as mc_color; x0 the first
+ * output word: c_v = 1 + floor(x0 / lambda_q32) when x0 < (k-1) lambda_q32,
+ * else 0.  lambda_q32 = 0 is mc_color.  Estimates from tables built with
+ * such colours must be given the same lambda_q32 (colour_bias_q32 of
+ * mc_estimate_params). */
+mc_status mc_color_biased(const mc_graph *g, int k, uint64_t seed, uint32_t lambda_q32, uint8_t *colors,
+                          void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Count tables (Section 2.1, Eq. 1; Section 3.2.1)                          */
@@ -180,6 +189,11 @@ mc_status mc_tables_status(const mc_tables *t, void *stream);
  * one).  Only sets that contain c_v (for c) or avoid it (for S) are stored. */
 mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,
                           int *entry_bytes);
+/* Non-zero entries of a level (which = 0: c, which = 1: S), counted on the
+ * device: the entries a zero-suppressed (succinct) table would keep
+ * (Section 3.2.1).  Synchronises `stream`. */
+mc_status mc_table_nonzeros(const mc_tables *t, int h, int which, int64_t *count, void *stream);
+
 /* Copy a whole level (n * row_entries * entry_bytes bytes) into dst (host or
  * device as dst_on_device says).  Level 1 of c is all ones and is produced on
  * the fly.  Synchronises `stream`. */
@@ -241,6 +255,11 @@ typedef struct {
     double eps, delta;     /* AGS accuracy, used when cbar <= 0 */
     int64_t batch;         /* AGS speculative batch; <= 0: automatic */
     int64_t node_lo, node_hi;  /* root nodes [node_lo, node_hi); node_hi <= 0: all nodes */
+    uint32_t colour_bias_q32;  /* lambda_q32 of the biased colouring the tables were built with
+                                  (0: uniform); the estimate divides by the probability
+                                  p = h! (C(k-1,h) lambda^h + C(k-1,h-1) lambda^(h-1) (1-(k-1) lambda))
+                                  that an h-node set is colourful, evaluated in that order in
+                                  double */
     int64_t star_samples;  /* round-skipped tables at h = k: uncoloured h-stars drawn (with the
                               same sample indices) to estimate the graphlets that only stars
                               span; their estimate is (S * hits*_i) / (sigma*_i * star_samples),

@@ -39,7 +39,7 @@ EXPORTED = [
     "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
     "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars", "mc_rebuild_tables",
-    "mc_tables_status",
+    "mc_tables_status", "mc_color_biased", "mc_table_nonzeros",
 ]
 
 
@@ -63,7 +63,8 @@ class EstimateParams(C.Structure):
     _fields_ = [("mode", C.c_int), ("h", C.c_int), ("seed", C.c_uint64),
                 ("first_index", C.c_uint64), ("samples", C.c_int64), ("cbar", C.c_int64),
                 ("eps", C.c_double), ("delta", C.c_double), ("batch", C.c_int64),
-                ("node_lo", C.c_int64), ("node_hi", C.c_int64), ("star_samples", C.c_int64)]
+                ("node_lo", C.c_int64), ("node_hi", C.c_int64), ("colour_bias_q32", C.c_uint32),
+                ("star_samples", C.c_int64)]
 
 
 class Request(C.Structure):
@@ -125,6 +126,8 @@ def load(path: str | None = None):
         lib.mc_server_free.restype = None
         lib.mc_star_total.argtypes = [P, C.c_int, P, P]
         lib.mc_rebuild_tables.argtypes = [P, P, P]
+        lib.mc_color_biased.argtypes = [P, C.c_int, u64, C.c_uint32, P, P]
+        lib.mc_table_nonzeros.argtypes = [P, C.c_int, C.c_int, C.POINTER(i64), P]
         lib.mc_tables_status.argtypes = [P, P]
         lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
         _lib = lib
@@ -265,12 +268,16 @@ class Graph:
             pass
 
 
-def color(graph: Graph, k: int, seed: int, out=None, stream=None):
-    """mc_color: counter-based uniform colouring, a device uint8 tensor."""
+def color(graph: Graph, k: int, seed: int, out=None, stream=None, bias_q32: int = 0):
+    """mc_color (or mc_color_biased with bias_q32 = lambda * 2^32 > 0):
+    counter-based colouring, a device uint8 tensor."""
     torch = _torch()
     if out is None:
         out = torch.empty(max(graph.n, 1), dtype=torch.uint8, device="cuda")
-    _check(load().mc_color(graph.handle, k, seed, _ptr(out), _stream_ptr(stream)))
+    if bias_q32:
+        _check(load().mc_color_biased(graph.handle, k, seed, bias_q32, _ptr(out), _stream_ptr(stream)))
+    else:
+        _check(load().mc_color(graph.handle, k, seed, _ptr(out), _stream_ptr(stream)))
     return out[: graph.n]
 
 
@@ -298,6 +305,12 @@ class Tables:
                                       None if own_memory else C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
+
+    def nonzeros(self, h: int, which: int = 0, stream=None) -> int:
+        """mc_table_nonzeros: non-zero entries of level h (0: c, 1: S)."""
+        out = C.c_int64()
+        _check(load().mc_table_nonzeros(self.handle, h, which, C.byref(out), _stream_ptr(stream)))
+        return out.value
 
     def rebuild(self, colors, stream=None):
         """mc_rebuild_tables: the whole build again for a new colouring (device
@@ -386,13 +399,14 @@ class Tables:
 
     def estimate(self, h: int, seed: int, samples: int, mode: int = MC_EST_UNIFORM,
                  first_index: int = 0, cbar: int = 0, eps: float = 0.0, delta: float = 0.0,
-                 batch: int = 0, node_range=(0, 0), star_samples: int = 0, stream=None):
+                 batch: int = 0, node_range=(0, 0), star_samples: int = 0, colour_bias_q32: int = 0,
+                 stream=None):
         """mc_estimate_counts: (estimates, hits, stats dict)."""
         ncls = num_classes(h)
         est = np.zeros(ncls, np.float64)
         hits = np.zeros(ncls, np.uint64)
         prm = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
-                             node_range[0], node_range[1], star_samples)
+                             node_range[0], node_range[1], colour_bias_q32, star_samples)
         st = EstimateStats()
         _check(load().mc_estimate_counts(self.handle, C.byref(prm), _ptr(est), _ptr(hits),
                                          C.byref(st), _stream_ptr(stream)))
@@ -518,9 +532,9 @@ class Server:
     def submit_estimate(self, table: int, h: int, seed: int, samples: int,
                         mode: int = MC_EST_UNIFORM, first_index: int = 0, cbar: int = 0,
                         eps: float = 0.0, delta: float = 0.0, batch: int = 0,
-                        node_range=(0, 0), star_samples: int = 0) -> int:
+                        node_range=(0, 0), star_samples: int = 0, colour_bias_q32: int = 0) -> int:
         e = EstimateParams(mode, h, seed, first_index, samples, cbar, eps, delta, batch,
-                           node_range[0], node_range[1], star_samples)
+                           node_range[0], node_range[1], colour_bias_q32, star_samples)
         r = Request(MC_REQ_ESTIMATE, table, 0, -1, 0, 0, 0, 0, 0, e)
         i = C.c_int64()
         _check(load().mc_server_submit(self.handle, C.byref(r), C.byref(i)))

@@ -1118,6 +1118,47 @@ extern "C" mc_status mc_build_tables_batch(int count, const mc_graph *const *gra
     return MC_OK;
 }
 
+// number of non-zero entries among n words (or pairs of words for u128)
+template <typename CT>
+__global__ void nonzeros_kernel(const CT *__restrict__ x, int64_t n, unsigned long long *count)
+{
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += x[i] != 0;
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+extern "C" mc_status mc_table_nonzeros(const mc_tables *t, int h, int which, int64_t *count, void *stream)
+{
+    return guarded([&] {
+        MC_REQUIRE(t && count, "NULL argument");
+        refresh_tables(t, (cudaStream_t)stream);
+        MC_REQUIRE(which == 0 || which == 1, "which must be 0 (c) or 1 (S)");
+        MC_REQUIRE(h >= 1 && h <= (which ? t->k - 1 : t->k), "h out of range");
+        MC_REQUIRE(!t->level_missing(h), "level h was skipped (round skipping)");
+        const int64_t n = t->g->n;
+        if (which == 0 && h == 1) { *count = n; return; }
+        const int64_t m = n * (which ? t->geo.Ws[h] : t->geo.Wc[h]);
+        cudaStream_t s = (cudaStream_t)stream;
+        Arena scratch(true);
+        scratch.alloc = t->arena.alloc;
+        scratch.stream = s;
+        unsigned long long *d = scratch.get<unsigned long long>(1), hc = 0;
+        MC_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), s));
+        const void *src = which ? t->S[h] : t->c[h];
+        if (m > 0) {
+            if (t->bits == 64)
+                MC_LAUNCH("nonzeros", s, nonzeros_kernel<uint64_t><<<grid_for(m, 256), 256, 0, s>>>((const uint64_t *)src, m, d));
+            else
+                MC_LAUNCH("nonzeros", s, nonzeros_kernel<u128><<<grid_for(m, 256), 256, 0, s>>>((const u128 *)src, m, d));
+        }
+        MC_CUDA(cudaMemcpyAsync(&hc, d, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+        *count = (int64_t)hc;
+    });
+}
+
 extern "C" mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,
                                      int *entry_bytes)
 {

@@ -144,6 +144,19 @@ __global__ void color_kernel(int64_t n, int k, uint64_t seed, uint8_t *colors)
     }
 }
 
+// Biased colouring (Section 3.4.3): the same Philox word; colour 1 + x / L
+// when x < (k-1) L, else 0 (probability L / 2^32 for each of colours 1..k-1).
+__global__ void color_biased_kernel(int64_t n, int k, uint64_t seed, uint32_t L, uint8_t *colors)
+{
+    const uint64_t rare = (uint64_t)(k - 1) * L;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)v, 0u, 0u, 0xC010u};
+        philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        colors[v] = (uint8_t)((uint64_t)c[0] < rare ? 1u + c[0] / L : 0u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // tracing
 // ---------------------------------------------------------------------------
@@ -429,5 +442,20 @@ extern "C" mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *
         if (g->n == 0) return;
         cudaStream_t s = (cudaStream_t)stream;
         MC_LAUNCH("color", s, color_kernel<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, k, seed, colors));
+    });
+}
+
+extern "C" mc_status mc_color_biased(const mc_graph *g, int k, uint64_t seed, uint32_t lambda_q32, uint8_t *colors,
+                                     void *stream)
+{
+    if (lambda_q32 == 0) return mc_color(g, k, seed, colors, stream);
+    return guarded([&] {
+        MC_REQUIRE(g && colors, "graph or colors is NULL");
+        MC_REQUIRE(k >= 2 && k <= 255, "k out of range");
+        MC_REQUIRE((uint64_t)(k - 1) * lambda_q32 <= 4294967296ull, "(k-1) lambda must be at most 1");
+        if (g->n == 0) return;
+        cudaStream_t s = (cudaStream_t)stream;
+        MC_LAUNCH("color", s, color_biased_kernel<<<grid_for(g->n, 256), 256, 0, s>>>(g->n, k, seed, lambda_q32,
+                                                                                      colors));
     });
 }

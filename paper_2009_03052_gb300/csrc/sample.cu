@@ -1089,6 +1089,23 @@ static double inv_colourful_prob(int k, int h)
     return num / den;
 }
 
+// 1 / p for the biased colouring (lambda = L / 2^32): an h-node set is
+// colourful with probability h! e_h(p_0, lambda, ..., lambda) =
+// h! (C(k-1,h) lambda^h + C(k-1,h-1) lambda^(h-1) p_0), p_0 = 1 - (k-1) lambda;
+// lambda and p_0 are exact doubles, the rest is evaluated in this order.
+static double inv_colourful_prob_biased(int k, int h, uint32_t L)
+{
+    if (L == 0) return inv_colourful_prob(k, h);
+    const double lam = (double)L / 4294967296.0;
+    const double p0 = (double)(4294967296ull - (uint64_t)(k - 1) * L) / 4294967296.0;
+    double lh1 = 1.0;
+    for (int i = 0; i < h - 1; ++i) lh1 *= lam;
+    double fact = 1.0;
+    for (int i = 2; i <= h; ++i) fact *= (double)i;
+    const double p = fact * ((double)binom(k - 1, h) * (lh1 * lam) + (double)binom(k - 1, h - 1) * (lh1 * p0));
+    return 1.0 / p;
+}
+
 }  // namespace mc
 
 using namespace mc;
@@ -1371,7 +1388,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         int *err = scratch.get<int>(2);
         MC_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
         mc_estimate_stats st{};
-        const double ip = inv_colourful_prob(t->k, h);
+        MC_REQUIRE((uint64_t)(t->k - 1) * p->colour_bias_q32 <= 4294967296ull, "(k-1) lambda must be at most 1");
+        const double ip = inv_colourful_prob_biased(t->k, h, p->colour_bias_q32);
         // round-skipped level k: sigma' replaces sigma, R replaces t, and the
         // graphlets only stars span come from uncoloured stars
         const bool skipped = t->skip_round && h == t->k;
