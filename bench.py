@@ -308,10 +308,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         if by is None:
             return None
         achieved = by / (ms / cnt / 1e3) / 1e9
-        return {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "traffic": TRAFFIC.get((wname, nm)), "algorithmic_bytes": int(by),
-                "bytes_model": src, "peak_source": peak_src, "avg_launch_ms": round(ms / cnt, 4)}
+        traffic = TRAFFIC.get((wname, nm))
+        out = {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+               "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+               "traffic": traffic, "algorithmic_bytes": int(by),
+               "bytes_model": src, "peak_source": peak_src, "avg_launch_ms": round(ms / cnt, 4)}
+        if traffic:  # the DRAM bytes of the ncu capture over this run's launch time
+            dram = traffic / (ms / cnt / 1e3) / 1e9
+            out["dram_gbs"] = round(dram, 1)
+            out["dram_frac"] = round(dram / hbm_peak, 4)
+        return out
 
     top = max(prof.items(), key=lambda x: x[1][0])[0] if prof else None
     roof = roofline(top) if top else None
