@@ -525,15 +525,20 @@ def run_rmat(args):
         T = M.Tables(G, col, k, bits)
         T.total(k)
         e[1].record(s)
-        t0 = time.perf_counter()
         est, hits, st = T.estimate(k, seed=i, samples=samples, mode=M.MC_EST_AGS, cbar=1000)
         e[2].record(s)
-        e[2].synchronize()
+        # uniform sampling of the same budget, for the AGS / uniform speed ratio
+        eu = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        eu[0].record(s)
+        T.estimate(k, seed=i, samples=samples)
+        eu[1].record(s)
+        eu[1].synchronize()
         T.free()
         if i >= args.warmup:
-            res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), st))
+            res.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), st, eu[0].elapsed_time(eu[1])))
     build_ms = statistics.median(r[0] for r in res)
     ags_ms = statistics.median(r[1] for r in res)
+    uni_ms = statistics.median(r[3] for r in res)
     entries = g.n * live_entries_per_node(k)
     st = res[-1][2]
     # per-kernel times of one more build (CUDA events of the library's profiler)
@@ -555,6 +560,8 @@ def run_rmat(args):
                    "cbar": 1000, "l2": "flushed between steps"},
         "build_ms": build_ms, "ags_ms": ags_ms,
         "ags_samples_per_s": st["samples"] / (ags_ms / 1e3), "ags_stats": st,
+        "uniform_samples_per_s": samples / (uni_ms / 1e3),
+        "ags_over_uniform_speed": (st["samples"] / ags_ms) / (samples / uni_ms),
         "build_kernels_ms": kern}), flush=True)
 
 
@@ -636,7 +643,6 @@ def run_serve(args):
 # (profiles/sample_kernel_chung_lu_1m_k5.md, profiles/gather_kernel_h3_chung_lu_1m_k5.md);
 # remove an entry when its kernel changes.
 TRAFFIC: dict = {
-    ("chung_lu_1m_k5", "sample"): 2_412_321_848,     # 1M samples, 2.083 GB read + 0.329 GB written
     ("chung_lu_1m_k5", "gather_h3"): 804_434_176,    # 0.737 GB read + 0.067 GB written
 }
 

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 
 // Sum the chunk partials of each hub into its S row.
 template <typename CT>
-__global__ void hub_reduce_kernel(const CT *__restrict__ partial, CT *__restrict__ dst,
+__global__ void hub_reduce_kernel(CT *__restrict__ partial, CT *__restrict__ dst,
                                   const uint32_t *__restrict__ hub_node,
                                   const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int Ws,
                                   int *err)
@@ -160,9 +160,14 @@ __global__ void hub_reduce_kernel(const CT *__restrict__ partial, CT *__restrict
         const int64_t hub = i / Ws;
         const int e = (int)(i - hub * Ws);
         const int64_t c0 = hub_chunk0[hub], nch = hub_chunk0[hub + 1] - c0;
-        const CT *p = partial + c0 * Ws + e * nch;
+        CT *p = partial + c0 * Ws + e * nch;
+        // the chunk sums become their inclusive prefix (the sampler
+        // binary-searches it); the last one is the hub's neighbour sum
         CT s = 0;
-        for (int64_t c = 0; c < nch; ++c) ovf |= add_ovf(s, p[c]);
+        for (int64_t c = 0; c < nch; ++c) {
+            ovf |= add_ovf(s, p[c]);
+            p[c] = s;
+        }
         dst[(int64_t)hub_node[hub] * Ws + e] = s;
     }
     if (ovf) atomicOr(err, ERR_OVERFLOW);
@@ -735,7 +740,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
             launch_gather<CT>(ga, grp, h, s);
             if (g->n_hubs) {
                 MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
-                    (const CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
+                    (CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
             }
         }
     }

@@ -172,7 +172,8 @@ struct mc_tables {
                                                // v's row of scol, relative to row_ptr[v]
     void *c[mc::MAXK + 1] = {nullptr};         // level h >= 2: n x Wc[h] counts
     void *S[mc::MAXK + 1] = {nullptr};         // level h <= k-1: n x Ws[h] counts
-    void *Sp[mc::MAXK + 1] = {nullptr};        // level h <= k-1: hub chunk partial sums, n_chunks x Ws[h]
+    void *Sp[mc::MAXK + 1] = {nullptr};        // level h <= k-1: per hub and S entry, the inclusive
+                                               // prefix of its chunk sums, n_chunks x Ws[h]
     mc::u128 *prefix[mc::MAXK + 1] = {nullptr};  // inclusive node prefix of level totals
     mc::u128 R[mc::MAXK + 1] = {0};            // rooted totals
     // root index of a level (node prefix, R, buckets): level k at build,

@@ -300,7 +300,7 @@ struct SampleArgs {
     int64_t n;
     const void *c[MAXK + 1];
     const void *S[MAXK + 1];
-    const void *Sp[MAXK + 1];   // hub chunk partial sums per level
+    const void *Sp[MAXK + 1];   // per level: inclusive prefix of each hub's chunk sums
     const int32_t *node_chunk0; // first chunk of a hub, -1 for other nodes
     int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
     int k, h;
@@ -373,67 +373,6 @@ __device__ __forceinline__ bool adjacent(const int64_t *row_ptr, const uint32_t 
     return lo < end && col[lo] == b;
 }
 
-__device__ __forceinline__ uint64_t warp_inclusive_scan(uint64_t x)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    return x;
-}
-__device__ __forceinline__ uint64_t shfl(uint64_t x, int src) { return __shfl_sync(0xffffffffu, x, src); }
-
-// Over items i = 0 .. len-1 in order, the first whose running sum of val(i)
-// exceeds q (-1 if none); `before` receives the running sum before it.  Up
-// to 32*IPL items per pass: lane l takes ceil(n/32) consecutive items, so
-// their loads are independent; a warp scan of the lane totals finds the
-// lane, the lane finds the item.  Exact integers: the result is that of a
-// flat scan in order.
-template <int IPL, typename V, typename F>
-__device__ __forceinline__ int64_t warp_first_exceeding(int64_t len, V q, F val, V &before)
-{
-    const int lane = threadIdx.x & 31;
-    V run = 0;
-    for (int64_t b = 0; b < len; b += 32 * IPL) {
-        const int64_t n = len - b < 32 * IPL ? len - b : 32 * IPL;
-        const int ipl = (int)((n + 31) >> 5);
-        const int64_t mine = b + (int64_t)lane * ipl;
-        V v[IPL];
-        V tot = 0;
-#pragma unroll
-        for (int i = 0; i < IPL; ++i) {
-            v[i] = 0;
-            if (i < ipl && mine + i < b + n) v[i] = val(mine + i);
-            tot += v[i];
-        }
-        const V incl = warp_inclusive_scan(tot);
-        const unsigned m = __ballot_sync(0xffffffffu, run + incl > q);
-        if (m) {
-            const int f = __ffs(m) - 1;
-            int64_t sel = -1;
-            V bf = 0;
-            if (lane == f) {
-                V c = run + incl - tot;
-                bool done = false;
-#pragma unroll
-                for (int i = 0; i < IPL; ++i) {
-                    if (!done && i < ipl) {
-                        if (c + v[i] > q) { sel = mine + i; bf = c; done = true; }
-                        else c += v[i];
-                    }
-                }
-            }
-            sel = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)sel, f);
-            before = shfl(bf, f);
-            return sel;
-        }
-        run += shfl(incl, 31);
-    }
-    return -1;
-}
-
 // Per-lane search: over items 0 .. len-1 in order, the first whose running
 // sum of val(i) exceeds q (-1 if none), `before` the running sum before it.
 // Items are loaded four at a time so that their loads are in flight
@@ -496,12 +435,11 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 
 // Lane-per-sample sampler: the 32 lanes of a warp draw 32 samples and walk
 // their h-1 decomposition steps in lockstep (every h-treelet has h-1 internal
-// decomposition nodes).  A lane does its own scalar work and short scans; a
-// hub's chunk search longer than SEQ_CHUNKS is done by the whole warp, one
-// lane's search after another.  CT: the tables' count type; V: the type of
-// the descent's weights, draws and running sums (64 bits when every level
-// total leaves room for beta, else 128 bits).
-constexpr int SEQ_CHUNKS = 64;
+// decomposition nodes).  A lane does its own scalar work, short scans and
+// binary searches (a hub's chunk by the prefix sums of its chunks).  CT: the
+// tables' count type; V: the type of the descent's weights, draws and
+// running sums (64 bits when every level total leaves room for beta, else
+// 128 bits).
 
 template <typename CT, typename V>
 __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ SampleArgs a)
@@ -513,7 +451,6 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
     if (a.hist)
         for (int i = threadIdx.x; i < a.ncls; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -623,7 +560,7 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
                 }
             }
             // ---- hub: the 64-neighbour chunk holding the answer, from the
-            // chunk partial sums (contiguous per hub and entry)
+            // inclusive prefix of its chunk sums (contiguous per hub and entry)
             // T'' one node: c(T''_{C''}, u) is 1 for the neighbours of the one
             // colour of C'' and 0 otherwise, so the answer is the (q+1)-th
             // neighbour of that colour in ascending id order: position q of
@@ -634,21 +571,18 @@ __global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ 
             if (chunked) spp = (const CT *)a.Sp[hb] + (int64_t)chunk0 * a.Ws[hb] + (int64_t)sidx * nch;
             int64_t ci = -1;
             CT bc = 0;
-            const bool coop = chunked && nch > SEQ_CHUNKS;
-            unsigned need = __ballot_sync(FULL, coop);
-            while (need) {
-                const int L = __ffs(need) - 1;
-                need &= need - 1;
-                const CT *sL = (const CT *)__shfl_sync(FULL, (unsigned long long)spp, L);
-                const int64_t nL = (int64_t)__shfl_sync(FULL, (unsigned long long)nch, L);
-                const CT qL = shfl(q, L);
-                CT bL;
-                const int64_t cL = warp_first_exceeding<4, CT>(nL, qL, [&](int64_t i) -> CT { return sL[i]; }, bL);
-                if (lane == L) { ci = cL; bc = bL; }
+            if (chunked) {
+                // the first chunk whose inclusive prefix exceeds q: a binary
+                // search of the hub's chunk prefix sums for this S entry
+                int64_t lo = 0, hi = nch - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (spp[mid] > q) hi = mid; else lo = mid + 1;
+                    rb += CB;
+                }
+                rb += 2 * CB;
+                if (spp[lo] > q) { ci = lo; bc = lo ? spp[lo - 1] : (CT)0; }
             }
-            if (chunked && !coop)
-                ci = lane_first_exceeding<CT>((int)nch, q, [&](int i) -> CT { rb += CB; return spp[i]; }, bc);
-            if (coop) rb += (uint64_t)CB * (uint64_t)(ci + 1);
             int64_t lo_e = e0, hi_e = e1;
             CT qq = q;
             if (chunked) {
