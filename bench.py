@@ -643,6 +643,7 @@ def run_serve(args):
 # (profiles/sample_kernel_chung_lu_1m_k5.md, profiles/gather_kernel_h3_chung_lu_1m_k5.md);
 # remove an entry when its kernel changes.
 TRAFFIC: dict = {
+    ("chung_lu_1m_k5", "sample"): 2_599_895_352,     # 1M samples, 2.153 GB read + 0.447 GB written
     ("chung_lu_1m_k5", "gather_h3"): 804_434_176,    # 0.737 GB read + 0.067 GB written
 }
 

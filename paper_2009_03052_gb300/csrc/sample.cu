@@ -442,7 +442,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 // 128 bits).
 
 template <typename CT, typename V>
-__global__ void __launch_bounds__(256, 4) sample_kernel(const __grid_constant__ SampleArgs a)
+__global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ SampleArgs a)
 {
     extern __shared__ unsigned int s_hist[];
     __shared__ SampleSmem sm;
