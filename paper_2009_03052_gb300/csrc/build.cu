@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
     const int64_t total = a.n * a.W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / a.W;
+        // node and output entry; 32-bit division when the level fits 2^32 entries
+        const int64_t v = total <= 0xffffffffll ? (int64_t)((uint32_t)t / (uint32_t)a.W) : t / a.W;
         const int o = (int)(t - v * a.W);
         if (a.zero_root_colors && a.zero_root_colors[v] != 0) {
             ((CT *)a.out)[t] = 0;
