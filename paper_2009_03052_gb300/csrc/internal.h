@@ -126,7 +126,7 @@ void refresh_tables(const mc_tables *t, cudaStream_t s, bool force = false);
 
 // Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
-// partial sums are added afterwards.
+// sums are added afterwards (and kept as their prefix for the sampler).
 constexpr int HUB_CHUNK = 64;
 
 }  // namespace mc
