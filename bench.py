@@ -72,13 +72,21 @@ def algorithmic_bytes(name: str, n: int, nnz: int, k: int, B: int):
         h = int(name[len("gather_h"):])
         return n * Wc[h] * B + n * Ws[h] * B + csr
     if name.startswith("merge_h"):
-        from oracle import catalog as cat  # shape sizes only (catalogue, no arithmetic)
+        import paper_2009_03052_gb300 as M
         h = int(name[len("merge_h"):])
-        c = cat.Catalog(k)
         used1, used2 = set(), set()
-        for g in range(c.first[h], c.first[h + 1]):
-            used1.add(c.size[c.left[g]])
-            used2.add(c.size[c.right[g]])
+        for code in M.shape_info(h)["code"]:
+            # s_T of the shape; T'' is the subtree of the first root child
+            bits = format(int(code), "0%db" % (2 * (h - 1)))
+            depth, end = 0, 0
+            for i, ch in enumerate(bits):
+                depth += 1 if ch == "1" else -1
+                if depth == 0:
+                    end = i + 1
+                    break
+            h2 = end // 2
+            used1.add(h - h2)
+            used2.add(h2)
         rd = sum(Wc[x] for x in used1 if x > 1) + sum(Ws[x] for x in used2)
         return n * (rd + Wc[h]) * B
     return None
