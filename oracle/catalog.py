@@ -4,7 +4,7 @@ Rooted treelet shapes on h <= 8 nodes, their bitstring encoding s_T, the
 canonical decomposition T -> (T', T'') with its multiplicity beta_T, and the
 unrooted shape of each rooting.
 
-* s_T (Section 3.2.1, "Treelet representation"): a DFS from the root writes
+* s_T (Section 3.2.1): a DFS from the root writes
   1 for every edge walked away from the root and 0 for every edge walked
   back; the children of a node are visited in the order of their own
   encodings.  The worked example of Figure 1 (root with a two-child subtree
@@ -12,8 +12,8 @@ unrooted shape of each rooting.
   comes first, i.e. children are visited in *decreasing* lexicographic
   order.  Shape ids within a size are ranks of s_T read as a 2(h-1)-bit
   unsigned integer, most significant bit first, ascending.
-* Decomposition (Eq. 1 and the merge of Section 3.2.1, "merging T' and T''
-  boils down to concatenating 1, s_T'', s_T'"): T'' is the subtree of the
+* Decomposition (Eq. 1, and the merge of Section 3.2.1, which writes a 1,
+  then s_T'', then s_T'): T'' is the subtree of the
   root's first (largest) child and T' is T with that subtree removed;
   beta_T is the number of root children whose subtree equals T''.
 * Unrooted shapes: the code of an unrooted tree is the smallest s_T over all
