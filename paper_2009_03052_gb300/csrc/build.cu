@@ -153,22 +153,34 @@ __global__ void hub_reduce_kernel(CT *__restrict__ partial, CT *__restrict__ dst
                                   const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int Ws,
                                   int *err)
 {
+    // a warp per (hub, S entry): the chunk sums, contiguous for the pair,
+    // become their inclusive prefix (the sampler binary-searches it) by warp
+    // scans of 32 chunks at a time; the last prefix is the hub's neighbour
+    // sum.  Any overflowing partial sum means the total overflows too.
     bool ovf = false;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = n_hubs * Ws;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = warp; i < total; i += nwarps) {
         const int64_t hub = i / Ws;
         const int e = (int)(i - hub * Ws);
         const int64_t c0 = hub_chunk0[hub], nch = hub_chunk0[hub + 1] - c0;
         CT *p = partial + c0 * Ws + e * nch;
-        // the chunk sums become their inclusive prefix (the sampler
-        // binary-searches it); the last one is the hub's neighbour sum
-        CT s = 0;
-        for (int64_t c = 0; c < nch; ++c) {
-            ovf |= add_ovf(s, p[c]);
-            p[c] = s;
+        CT carry = 0;
+        for (int64_t b = 0; b < nch; b += 32) {
+            const int64_t c = b + lane;
+            CT x = c < nch ? p[c] : (CT)0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const CT y = shfl_up(x, d);
+                if (lane >= d) ovf |= add_ovf(x, y);
+            }
+            ovf |= add_ovf(x, carry);
+            if (c < nch) p[c] = x;
+            carry = shfl(x, 31);
         }
-        dst[(int64_t)hub_node[hub] * Ws + e] = s;
+        if (lane == 0) dst[(int64_t)hub_node[hub] * Ws + e] = carry;
     }
     if (ovf) atomicOr(err, ERR_OVERFLOW);
 }
@@ -740,7 +752,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
             while (grp < G.Ws[h] && grp < 32) grp <<= 1;
             launch_gather<CT>(ga, grp, h, s);
             if (g->n_hubs) {
-                MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
+                MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h] * 32, 256), 256, 0, s>>>(
                     (CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
             }
         }

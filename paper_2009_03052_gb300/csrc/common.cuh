@@ -95,6 +95,14 @@ __device__ __forceinline__ uint64_t shfl_xor(uint64_t x, int d)
 {
     return __shfl_xor_sync(0xffffffffu, x, d);
 }
+__device__ __forceinline__ uint64_t shfl_up(uint64_t x, int d)
+{
+    return __shfl_up_sync(0xffffffffu, x, d);
+}
+__device__ __forceinline__ uint64_t shfl(uint64_t x, int src)
+{
+    return __shfl_sync(0xffffffffu, x, src);
+}
 __device__ __forceinline__ u128 shfl(u128 x, int src)
 {
     uint64_t lo = __shfl_sync(0xffffffffu, (uint64_t)x, src);
