@@ -349,7 +349,9 @@ mc_status mc_server_submit(mc_server *server, const mc_request *request, int64_t
  * results are delivered once. */
 mc_status mc_server_wait(mc_server *server, int64_t id, uint32_t *nodes, int32_t *classes, double *est,
                          uint64_t *hits, double *queue_us, double *latency_us);
-/* Stop the workers after their current requests and free the server. */
+/* Stop the workers after their current requests and free the server.
+ * Requests still queued are dropped; no thread may be waiting in
+ * mc_server_wait on this server (its wait would never end). */
 void mc_server_free(mc_server *server);
 
 /* ------------------------------------------------------------------------ */

@@ -60,25 +60,21 @@ static void run_request(mc_server *sv, Request &q, cudaStream_t s)
 {
     const mc_tables *t = sv->tables[q.r.table];
     if (q.r.kind == MC_REQ_SAMPLE) {
-        uint32_t *dn = nullptr;
-        int32_t *dc = nullptr;
         const int64_t n = q.r.count;
-        MC_CUDA(cudaMallocAsync(&dn, (size_t)std::max<int64_t>(n, 1) * q.r.h * 4, s));
-        MC_CUDA(cudaMallocAsync(&dc, (size_t)std::max<int64_t>(n, 1) * 4, s));
+        Arena out(true);  // stream-ordered device outputs, freed when the request is done
+        out.stream = s;
+        uint32_t *dn = out.get<uint32_t>((size_t)std::max<int64_t>(n, 1) * q.r.h);
+        int32_t *dc = out.get<int32_t>((size_t)std::max<int64_t>(n, 1));
         mc_status st = mc_sample_range(t, q.r.h, q.r.unrooted_shape, q.r.node_lo, q.r.node_hi, q.r.seed,
                                        q.r.first_index, n, dn, nullptr, nullptr, dc, (void *)s);
-        if (st == MC_OK) {
-            q.nodes.resize((size_t)n * q.r.h);
-            q.classes.resize((size_t)n);
-            if (n) {
-                MC_CUDA(cudaMemcpyAsync(q.nodes.data(), dn, q.nodes.size() * 4, cudaMemcpyDeviceToHost, s));
-                MC_CUDA(cudaMemcpyAsync(q.classes.data(), dc, q.classes.size() * 4, cudaMemcpyDeviceToHost, s));
-            }
-        }
-        cudaFreeAsync(dn, s);
-        cudaFreeAsync(dc, s);
-        MC_CUDA(cudaStreamSynchronize(s));
         if (st != MC_OK) throw Error(st, mc_last_error());
+        q.nodes.resize((size_t)n * q.r.h);
+        q.classes.resize((size_t)n);
+        if (n) {
+            MC_CUDA(cudaMemcpyAsync(q.nodes.data(), dn, q.nodes.size() * 4, cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(q.classes.data(), dc, q.classes.size() * 4, cudaMemcpyDeviceToHost, s));
+        }
+        MC_CUDA(cudaStreamSynchronize(s));
     } else {
         const int nc = mc_num_classes(q.r.est.h);
         if (nc < 0) throw Error(MC_E_INVALID, mc_last_error());
@@ -156,7 +152,18 @@ extern "C" mc_status mc_server_create(const mc_tables *const *tables, int n_tabl
         sv->budget = memory_budget;
         for (int i = 0; i < slots; ++i) sv->workers.emplace_back(worker, sv);
     });
-    if (st != MC_OK) { delete sv; return st; }
+    if (st != MC_OK) {
+        if (sv) {  // stop the workers started before the failure
+            {
+                std::lock_guard<std::mutex> lock(sv->mu);
+                sv->stop = true;
+            }
+            sv->cv.notify_all();
+            for (auto &w : sv->workers) w.join();
+        }
+        delete sv;
+        return st;
+    }
     *out = sv;
     return MC_OK;
 }
