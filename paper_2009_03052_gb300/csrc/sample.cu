@@ -360,19 +360,6 @@ __device__ __forceinline__ unsigned deposit(unsigned im, unsigned rest)
     return out;
 }
 
-__device__ __forceinline__ bool adjacent(const int64_t *row_ptr, const uint32_t *col, uint32_t a, uint32_t b)
-{
-    int64_t lo = row_ptr[a], hi = row_ptr[a + 1];
-    const int64_t lb = row_ptr[b], hb = row_ptr[b + 1];
-    if (hb - lb < hi - lo) { lo = lb; hi = hb; b = a; }
-    const int64_t end = hi;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (col[mid] < b) lo = mid + 1; else hi = mid;
-    }
-    return lo < end && col[lo] == b;
-}
-
 // Per-lane search: over items 0 .. len-1 in order, the first whose running
 // sum of val(i) exceeds q (-1 if none), `before` the running sum before it.
 // Items are loaded four at a time so that their loads are in flight
