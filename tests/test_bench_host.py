@@ -1,0 +1,47 @@
+"""Host-side pieces of the benchmark (no GPU): the entry counts behind the
+metric and the compulsory-bytes model of the build kernels."""
+import math
+
+import bench
+
+
+def test_live_entries_per_node():
+    # r_h C(k-1, h-1) summed over h: the colour-relative row widths
+    assert [bench.live_entries_per_node(k) for k in range(4, 9)] == [14, 42, 131, 420, 1376]
+
+
+def test_geometry_widths():
+    Wc, Ws = bench.geometry(8)
+    assert sum(Wc.values()) == 1376 and sum(Ws.values()) == 615
+    Wc, Ws = bench.geometry(5)
+    assert [Wc[h] for h in range(1, 6)] == [1, 4, 12, 16, 9]
+    assert [Ws[h] for h in range(1, 5)] == [4, 6, 8, 4]
+
+
+def test_gather_and_merge_bytes():
+    import paper_2009_03052_gb300 as M
+    M.load()
+    n, nnz, B = 1000, 8000, 8
+    csr = 8 * (n + 1) + 4 * nnz + n
+    assert bench.algorithmic_bytes("gather_h3", n, nnz, 5, B) == n * (12 + 8) * B + csr
+    # merge of level 5: reads c rows of the T' sizes and S rows of the T''
+    # sizes the level's decompositions use, writes the level-5 row
+    Wc, Ws = bench.geometry(5)
+    used1, used2 = set(), set()
+    for s in M.shape_info(5)["code"]:
+        bits = format(int(s), "08b")
+        depth = 0
+        for i, ch in enumerate(bits):
+            depth += 1 if ch == "1" else -1
+            if depth == 0:
+                used2.add((i + 1) // 2)
+                used1.add(5 - (i + 1) // 2)
+                break
+    want = n * (sum(Wc[x] for x in used1 if x > 1) + sum(Ws[x] for x in used2) + Wc[5]) * B
+    assert bench.algorithmic_bytes("merge_h5", n, nnz, 5, B) == want
+    assert math.isclose(want / n / B, 63)  # c2 4 + c3 12 + c4 16 + S1 4 + S2 6 + S3 8 + S4 4 + out 9
+
+
+def test_job_throughput_single_rank():
+    ms, v = bench.job_throughput(1000.0, 2.0, 1)
+    assert ms == 2.0 and v == 1000.0 / 0.002
