@@ -49,6 +49,16 @@ def workload_graph(small: bool):
     return synth.chung_lu_1m(), "chung_lu_1m_k5"
 
 
+def workload_config(graph, wname: str, k: int, samples: int, args, world: int) -> dict:
+    """The `config` of the default workload's JSON line (both arms)."""
+    return {"workload": wname, "n": int(graph.n), "m": int(graph.nnz) // 2, "k": k, "count_bits": BITS,
+            "samples_per_step": samples, "zero_root": bool(args.zero_root),
+            "skip_round": bool(args.skip_round),
+            "star_samples_per_step": samples if args.skip_round else 0,
+            "l2": "flushed between steps (256 MiB write, outside the per-step events)",
+            "parallelism": f"replicas{world}"}
+
+
 def live_entries_per_node(k: int) -> int:
     return sum(R_H[h] * math.comb(k - 1, h - 1) for h in range(1, k + 1))
 
@@ -161,10 +171,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
-def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int):
+def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int, step_samples: int = SAMPLES):
     """Time the oracle on the workload: its table build on the full graph
     plus n_samples uniform samples with classification; the sampling time
-    is scaled to the step's 1M samples."""
+    is scaled to the step's step_samples."""
     import oracle
     oracle.build()
     oracle.class_codes(k)  # class list precomputed outside the timing
@@ -176,7 +186,7 @@ def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int):
     T.estimate_uniform(k, seed=seed, n_samples=n_samples)
     t2 = time.perf_counter()
     build_s, samp_s = t1 - t0, t2 - t1
-    step_s = build_s + samp_s * (SAMPLES / n_samples)
+    step_s = build_s + samp_s * (step_samples / n_samples)
     entries = graph.n * live_entries_per_node(k)
     return {"value": entries / step_s, "build_s": build_s, "sample_s": samp_s,
             "step_s_equiv": step_s}
@@ -192,18 +202,20 @@ def run_reference(args, rank: int, world: int):
     warm = synth.chung_lu_scaled(5000, seed=1)
     for i in range(args.warmup):
         oracle_step_rate(warm, K, 100, 100 + i, threads)
-    res = [oracle_step_rate(graph, K if not args.small else 4, n_samp, 10 + i, threads)
+    step_samples = SAMPLES if not args.small else 10_000
+    res = [oracle_step_rate(graph, K if not args.small else 4, n_samp, 10 + i, threads, step_samples)
            for i in range(args.steps)]
     val = statistics.median(r["value"] for r in res)
     step_ms = statistics.median(r["step_s_equiv"] for r in res) * 1e3
     sample = (f"oracle build of the full {wname} graph plus {n_samp} samples per step; "
-              f"sampling time scaled to {SAMPLES} samples")
+              f"sampling time scaled to {step_samples} samples")
     line = {
         "impl": "reference", "metric": "DP table entries/s", "value": val,
         "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u128", "data": "synthetic",
-        "config": {"workload": wname, "k": K, "count_bits": BITS, "samples_per_step": SAMPLES},
+        "config": workload_config(graph, wname, K if not args.small else 4, SAMPLES if not args.small else 10_000,
+                                  args, world),
         "cpu_baseline": {"value": val, "unit": "entries/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0,
@@ -365,7 +377,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         n_samp = 1000 if not args.small else 10_000
-        r = oracle_step_rate(graph, k, n_samp, 5, threads)
+        r = oracle_step_rate(graph, k, n_samp, 5, threads, samples)
         cpu = {"value": r["value"], "unit": "entries/s", "cores": threads, "kind": "oracle",
                "sample": (f"oracle build of the full {wname} graph ({r['build_s']:.1f} s) plus "
                           f"{n_samp} samples ({r['sample_s']:.2f} s), sampling scaled to "
@@ -380,12 +392,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": wname, "n": n, "m": nnz // 2, "k": k, "count_bits": BITS,
-                   "samples_per_step": samples, "zero_root": args.zero_root,
-                   "skip_round": args.skip_round,
-                   "star_samples_per_step": samples if args.skip_round else 0,
-                   "l2": "flushed between steps (256 MiB write, "
-                   "outside the per-step events)", "parallelism": f"replicas{world}"},
+        "config": workload_config(graph, wname, k, samples, args, world),
         "samples_per_s": samples * args.steps * world / (total_ms / 1e3),
         "phases_ms": {"build": round(build_ms, 3), "sample_classify_estimate": round(sample_ms, 3)},
         "build_entries_per_s": entries / (build_ms / 1e3),
