@@ -366,6 +366,15 @@ int mc_num_classes(int h);         /* connected h-node graphs; -1 on error */
  * ids of T' and T'' (-1 for h = 1).  Host arrays of mc_num_shapes(h). */
 mc_status mc_shape_info(int h, uint32_t *code, int32_t *unrooted, int32_t *beta, int32_t *left,
                         int32_t *right);
+/* The level-k decompositions of round skipping (MC_BUILD_SKIP_ROUND,
+ * Section 3.3.2), 4 <= k <= 8: per rooted k-shape (id order), beta_T and the
+ * sizes and ids of T' and T'' of its balanced decomposition, or -1 for the
+ * shapes that are not counted (host arrays of mc_num_shapes(k)); and per
+ * unrooted k-shape, a_j, the rooted copies the level-k table holds for each
+ * copy (host array of mc_num_unrooted(k); 0 for the star).  Any array may be
+ * NULL. */
+mc_status mc_skip_round_info(int k, int32_t *beta, int32_t *left_size, int32_t *left,
+                             int32_t *right_size, int32_t *right, int32_t *copies);
 /* Canonical adjacency words of the connected h-node graphs, ascending (host
  * uint32[mc_num_classes(h)]).  Word of a labelled graph: pairs (i, j), i < j,
  * in lexicographic order, the first pair in the most significant of the

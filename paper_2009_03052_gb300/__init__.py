@@ -39,7 +39,7 @@ EXPORTED = [
     "mc_profile_read", "mc_launch_count", "mc_estimate_uniform_noalloc", "mc_total_range",
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
     "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars", "mc_rebuild_tables",
-    "mc_tables_status", "mc_color_biased", "mc_table_nonzeros",
+    "mc_tables_status", "mc_color_biased", "mc_table_nonzeros", "mc_skip_round_info",
 ]
 
 
@@ -128,6 +128,7 @@ def load(path: str | None = None):
         lib.mc_rebuild_tables.argtypes = [P, P, P]
         lib.mc_color_biased.argtypes = [P, C.c_int, u64, C.c_uint32, P, P]
         lib.mc_table_nonzeros.argtypes = [P, C.c_int, C.c_int, C.POINTER(i64), P]
+        lib.mc_skip_round_info.argtypes = [C.c_int, P, P, P, P, P, P]
         lib.mc_tables_status.argtypes = [P, P]
         lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
         _lib = lib
@@ -453,6 +454,17 @@ def shape_info(h: int) -> dict:
     _check(load().mc_shape_info(h, _ptr(code), *[_ptr(a) for a in arrs]))
     return {"code": code, "unrooted": arrs[0], "beta": arrs[1], "left": arrs[2],
             "right": arrs[3]}
+
+
+def skip_round_info(k: int) -> dict:
+    """mc_skip_round_info: the balanced level-k decompositions of round
+    skipping and the rooted copies a_j per unrooted k-shape."""
+    r, nu = num_shapes(k), num_unrooted(k)
+    arrs = [np.zeros(r, np.int32) for _ in range(5)]
+    copies = np.zeros(nu, np.int32)
+    _check(load().mc_skip_round_info(k, *[_ptr(a) for a in arrs], _ptr(copies)))
+    return {"beta": arrs[0], "left_size": arrs[1], "left": arrs[2], "right_size": arrs[3],
+            "right": arrs[4], "copies": copies}
 
 
 def class_codes(h: int) -> np.ndarray:

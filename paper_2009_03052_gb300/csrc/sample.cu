@@ -1067,6 +1067,27 @@ extern "C" mc_status mc_shape_info(int h, uint32_t *code, int32_t *unrooted, int
     });
 }
 
+extern "C" mc_status mc_skip_round_info(int k, int32_t *beta, int32_t *left_size, int32_t *left,
+                                        int32_t *right_size, int32_t *right, int32_t *copies)
+{
+    return guarded([&] {
+        MC_REQUIRE(k >= 4 && k <= MAXK, "k must be in 4..8");
+        const ShapeCatalog &cat = shape_catalog();
+        const Programs &P = programs(k, true);
+        for (int i = 0; i < cat.r[k]; ++i) {
+            const int g = cat.gid(k, i);
+            const int l = P.bal_left[g], r = P.bal_right[g];
+            if (beta) beta[i] = l < 0 ? -1 : P.bal_beta[g];
+            if (left_size) left_size[i] = l < 0 ? -1 : cat.shapes[l].size;
+            if (left) left[i] = l < 0 ? -1 : cat.shapes[l].local;
+            if (right_size) right_size[i] = r < 0 ? -1 : cat.shapes[r].size;
+            if (right) right[i] = r < 0 ? -1 : cat.shapes[r].local;
+        }
+        if (copies)
+            for (int j = 0; j < cat.n_unrooted[k]; ++j) copies[j] = P.copies[j];
+    });
+}
+
 extern "C" mc_status mc_class_codes(int h, uint32_t *codes)
 {
     return guarded([&] {

@@ -50,3 +50,26 @@ def test_errors_without_device(motif):
     st = motif.load().mc_build_tables(None, None, 4, 64, 0, None, None, None)
     assert st == motif.MC_E_INVALID
     assert b"NULL" in motif.load().mc_last_error()
+
+
+def test_skip_round_programs_match_the_oracle_catalogue():
+    # the library's balanced level-k decompositions and a_j (host code)
+    # against the oracle's, written independently from Section 3.3.2
+    import paper_2009_03052_gb300 as M
+    M.load()
+    from oracle import catalog as cat
+    for k in range(4, 9):
+        info = M.skip_round_info(k)
+        shapes = cat.rooted_shapes(k)
+        for i, s in enumerate(shapes):
+            d = cat.balanced_decompose(s, k)
+            if d is None:
+                assert info["beta"][i] == -1 and info["left"][i] == -1 and info["right"][i] == -1
+                continue
+            a, b, beta = d
+            na, nb = len(a) // 2 + 1, len(b) // 2 + 1
+            assert info["beta"][i] == beta, (k, s)
+            assert (info["left_size"][i], info["right_size"][i]) == (na, nb), (k, s)
+            assert info["left"][i] == cat.rooted_shapes(na).index(a), (k, s)
+            assert info["right"][i] == cat.rooted_shapes(nb).index(b), (k, s)
+        assert list(info["copies"]) == cat.Catalog(k, skip_round=True).copies_divisor(k)
