@@ -52,7 +52,7 @@ def _chi2_ok(observed: Counter, expected_num: Counter, total: int, N: int) -> bo
     return chi2 < dof + 6.0 * math.sqrt(2.0 * dof)
 
 
-@pytest.mark.parametrize("k,seed", [(3, 1), (4, 2), (5, 3)])
+@pytest.mark.parametrize("k,seed", [(3, 1), (4, 2), (5, 3), (6, 4)])
 def test_sampler_is_uniform_over_colourful_treelets(oracle, k, seed):
     g = synth.erdos_renyi(9, 4.0, seed=seed)
     colors = synth.balanced_colors(g.n, k, seed=seed)

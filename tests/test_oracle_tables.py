@@ -207,3 +207,13 @@ def test_star_totals_closed_form_any_graph(oracle):
     assert T.total(2)[1] == stars[2]
     for h in range(3, k + 1):
         assert T.total(h, cat.unrooted_id("10" * (h - 1)))[1] == stars[h]
+
+
+@pytest.mark.parametrize("k", [7, 8])
+def test_tables_k7_k8_brute_force(oracle, k):
+    # the treelet sizes of the R-MAT (k = 7) and serving (k = 8) workloads
+    g = synth.erdos_renyi(k + 2, 4.0, seed=k)
+    colors = synth.balanced_colors(g.n, k, seed=k)
+    T = oracle.Tables(g, colors, k, 128, nthreads=2)
+    for h in (k - 1, k):
+        assert _table_dict(T, h) == brute.treelet_counts(g, colors, h), h
