@@ -73,3 +73,20 @@ def test_skip_round_programs_match_the_oracle_catalogue():
             assert info["left"][i] == cat.rooted_shapes(na).index(a), (k, s)
             assert info["right"][i] == cat.rooted_shapes(nb).index(b), (k, s)
         assert list(info["copies"]) == cat.Catalog(k, skip_round=True).copies_divisor(k)
+
+
+def test_header_is_plain_c_and_cpp(tmp_path):
+    # the boundary is a C ABI: the header compiles as C99 and as C++11
+    import os
+    import shutil
+    import subprocess
+    import pytest
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    for cc, std, ext in (("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not installed")
+        src = tmp_path / f"t.{ext}"
+        src.write_text('#include "motif.h"\nint main(void) { return MC_OK; }\n')
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
