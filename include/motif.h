@@ -6,7 +6,7 @@
  * sampling": colour the graph (Section 2.1), build the exact colourful
  * treelet count tables c(T_C, v) by the dynamic program of Eq. (1), sample
  * colourful treelets uniformly (Section 2.2) or adaptively (Algorithm AGS,
- * Section 4.1), classify the induced graphlets (Section 4.3.3) and estimate
+ * Section 4.1), classify the induced graphlets (Section 4.4.3) and estimate
  * graphlet counts.
  *
  * Conventions for every entry point:
@@ -23,7 +23,7 @@
  *    value that does not fit the count width (a table entry, a neighbour sum,
  *    a merge numerator or a level total) makes the call fail with
  *    MC_E_OVERFLOW; nothing wraps.
- *  - Graphs are simple and undirected (Section 1.2): n < 2^32 nodes, CSR with
+ *  - Graphs are simple and undirected (Section 1.3): n < 2^32 nodes, CSR with
  *    symmetric, sorted, duplicate-free, loop-free adjacency lists.
  *  - 2 <= k <= 8 colours; treelets and graphlets have h <= k nodes.
  */
@@ -86,7 +86,7 @@ mc_status mc_graph_info(const mc_graph *g, int64_t *n, int64_t *nnz, int64_t *ma
  * first word of Philox4x32-10 (Salmon et al., SC 2011) at key = seed
  * (low word first) and counter = (v, 0, 0, 0xC010). */
 mc_status mc_color(const mc_graph *g, int k, uint64_t seed, uint8_t *colors, void *stream);
-/* Biased colouring (Section 3.4.3): colours 1..k-1 each with probability
+/* Biased colouring (Section 3.5): colours 1..k-1 each with probability
  * lambda = lambda_q32 / 2^32, colour 0 with 1 - (k-1) lambda ((k-1) lambda
  * <= 1, else MC_E_INVALID).  Same counter and key as mc_color; x0 the first
  * output word: c_v = 1 + floor(x0 / lambda_q32) when x0 < (k-1) lambda_q32,
@@ -282,12 +282,12 @@ mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *param
                              uint64_t *hits, mc_estimate_stats *stats, void *stream);
 
 /* Uniform estimation that allocates no device memory, for callers that
- * cannot allocate: code running while a stream is being captured into a CUDA
- * graph (cudaMalloc is not allowed there), serving loops that hand every
- * byte of device memory to their own pool up front, and latency-critical
- * loops that must not hit cudaMalloc's implicit synchronisation.  The paper
- * has no counterpart: it computes the same result as mc_estimate_counts in
- * MC_EST_UNIFORM mode (same samples, same hits, same estimates).
+ * cannot allocate: serving loops that hand every byte of device memory to
+ * their own pool up front (a cudaMalloc would fail or take memory the pool
+ * counts on), and latency-critical loops that must not hit cudaMalloc's
+ * implicit device synchronisation.  The paper has no counterpart: it
+ * computes the same result as mc_estimate_counts in MC_EST_UNIFORM mode
+ * (same samples, same hits, same estimates).
  *  - Its device scratch (histogram, sigma and estimate arrays, error flags)
  *    is one static array of the library, sized for at most 12288 graphlet
  *    classes (about 290 KB), which every GPU that loads the library holds
@@ -299,7 +299,9 @@ mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *param
  *    (mc_sigma(h), mc_num_classes(h) with mc_sigma, or mc_estimate_counts
  *    create it); otherwise MC_E_INVALID, since creating it allocates.  For
  *    h < k the same holds for the level's root index (mc_total(t, h, -1, ...)
- *    or any sampling at that h creates it).
+ *    or any sampling at that h creates it), and after mc_rebuild_tables an
+ *    index of such a level made before the rebuild is refused with
+ *    MC_E_INVALID until mc_total(t, h, ...) remakes it.
  *  - All calls share the one scratch array, cleared at the start of each
  *    call: calls whose work overlaps on the GPU (other streams, other host
  *    threads) race and must be serialised by the caller.
@@ -313,9 +315,13 @@ mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint64_t seed, 
 /* A server keeps built tables on the device and runs sample and estimate
  * requests on a pool of `slots` workers, each with its own CUDA stream.
  * Requests queue in arrival order; the first queued request starts as soon
- * as a worker is idle and its device buffers fit `memory_budget` bytes (0:
- * half of the free device memory at creation; a request larger than the
- * budget runs alone).  Requests that arrive while others run are admitted as
+ * as a worker is idle and the device bytes it will allocate (outputs,
+ * scratch, and the root or star indices it creates; for AGS a root index per
+ * treelet shape and one batch of class ids) fit the device's free memory at
+ * that moment on top of what the running requests were charged, and, when
+ * `memory_budget` is not 0, fit that cap next to them.  With no request
+ * running the head is admitted regardless (if it does not fit the device it
+ * fails alone with MC_E_NOMEM).  Requests that arrive while others run are admitted as
  * workers and memory free up, and their work overlaps on the device.  A
  * request's result depends only on the tables, its seed and its sample
  * indices: it is the same alone and in any mix.  The tables must outlive the

@@ -143,7 +143,7 @@ def color(n: int, k: int, seed: int) -> np.ndarray:
 
 
 def color_biased(n: int, k: int, seed: int, bias_q32: int) -> np.ndarray:
-    """Biased colouring (Section 3.4.3): colours 1..k-1 with probability
+    """Biased colouring (Section 3.5): colours 1..k-1 with probability
     lambda = bias_q32 / 2^32 each, colour 0 otherwise."""
     out = np.zeros(max(n, 1), np.uint8)
     _check(_load().oc_color_biased(n, k, seed, bias_q32, out))
@@ -186,7 +186,7 @@ def class_of_word(h: int, word: int) -> int:
 
 
 def spanning_trees(h: int, word: int) -> int:
-    """sigma by Kirchhoff's matrix-tree theorem (Section 4.3.3)."""
+    """sigma by Kirchhoff's matrix-tree theorem (Section 4.4.3)."""
     return int(_load().oc_spanning_trees(h, word))
 
 
@@ -196,7 +196,7 @@ _sigma_cache: dict[int, tuple[np.ndarray, np.ndarray]] = {}
 def sigma(h: int) -> tuple[np.ndarray, np.ndarray]:
     """(sigma_i [classes], sigma_ij [classes x unrooted shapes]) for h-node
     graphlets; sigma_i by Kirchhoff, sigma_ij by the distinct-colour build
-    (Section 4.3.3)."""
+    (Section 4.4.3)."""
     if h not in _sigma_cache:
         codes = class_codes(h)
         s_i = np.array([spanning_trees(h, int(w)) for w in codes], np.int64)

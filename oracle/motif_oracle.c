@@ -15,7 +15,7 @@
  * of operations written out; build with -ffp-contract=off.
  *
  * Parallelism: the build loops over nodes with a plain thread pool, one
- * node per task, as the paper's build does (Section 3.4.4).  Nothing else
+ * node per task, as the paper's build does (Section 3.4.3).  Nothing else
  * is reordered, blocked or fused beyond the formulas cited at each step.
  */
 #include <stdint.h>
@@ -62,7 +62,7 @@ void oc_color(int64_t n, int k, uint64_t seed, uint8_t *colors)
     }
 }
 
-/* Biased colouring (Section 3.4.3): colours 1..k-1 each with probability
+/* Biased colouring (Section 3.5): colours 1..k-1 each with probability
  * lambda = L / 2^32, colour 0 with 1 - (k-1) lambda; (k-1) L <= 2^32.  The
  * same counter as above; x = x0: colour 1 + floor(x / L) when x < (k-1) L,
  * else 0.  L = 0 is the uniform colouring above. */
@@ -547,7 +547,7 @@ static int sample_one(const oc_tables *t, const root_index *ri, uint64_t seed, u
 }
 
 /* ------------------------------------------------------------------------ */
-/* Graphlet classes (Section 4.3.3)                                          */
+/* Graphlet classes (Section 4.4.3)                                          */
 /* Adjacency word: the pairs (i, j), i < j, of the h labels in lexicographic */
 /* order, first pair in the most significant of the C(h,2) bits.  Canonical  */
 /* code: the smallest word over all h! relabelings.  Class id: rank of the   */
@@ -839,7 +839,7 @@ int oc_sample_stars(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
 }
 
 /* ------------------------------------------------------------------------ */
-/* Spanning trees (Section 4.3.3)                                            */
+/* Spanning trees (Section 4.4.3)                                            */
 /* ------------------------------------------------------------------------ */
 
 /* sigma_i by Kirchhoff's matrix-tree theorem: the determinant of the
@@ -958,7 +958,7 @@ static double inv_colorful_prob(int k, int h)
 /* 1 / p under the biased colouring: an h-node set is colourful when its
  * colours are distinct, with probability h! e_h(p_0, lambda, ..., lambda) =
  * h! (C(k-1,h) lambda^h + C(k-1,h-1) lambda^(h-1) p_0), p_0 = 1 - (k-1) lambda
- * (Section 3.4.3 gives the leading terms j! lambda^j and j! lambda^(j-1)).
+ * (Section 3.5 gives the leading terms j! lambda^j and j! lambda^(j-1)).
  * lambda and p_0 are exact doubles; the rest is evaluated in this order. */
 static double inv_colorful_prob_biased(int k, int h, uint32_t L)
 {

@@ -144,7 +144,7 @@ __global__ void color_kernel(int64_t n, int k, uint64_t seed, uint8_t *colors)
     }
 }
 
-// Biased colouring (Section 3.4.3): the same Philox word; colour 1 + x / L
+// Biased colouring (Section 3.5): the same Philox word; colour 1 + x / L
 // when x < (k-1) L, else 0 (probability L / 2^32 for each of colours 1..k-1).
 __global__ void color_biased_kernel(int64_t n, int k, uint64_t seed, uint32_t L, uint8_t *colors)
 {

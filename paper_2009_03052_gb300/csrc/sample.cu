@@ -1,4 +1,4 @@
-// sample.cu -- graphlet classes (Section 4.3.3), uniform and shape-restricted
+// sample.cu -- graphlet classes (Section 4.4.3), uniform and shape-restricted
 // colourful treelet sampling (Section 2.2; sample(T) of Section 4.1), the
 // uniform estimator (Section 2.2) and adaptive graphlet sampling (Algorithm
 // AGS, Section 4.1).
@@ -182,7 +182,7 @@ ClassCatalog *class_catalog(int h)
     return class_catalog_locked(h);
 }
 
-// sigma_ij by the paper's recipe (Section 4.3.3): build the tables of every
+// sigma_ij by the paper's recipe (Section 4.4.3): build the tables of every
 // class graph with each node its own colour; the colourful h-treelets are
 // then exactly the spanning trees.  All classes go through one build, as a
 // disjoint union.
@@ -1588,8 +1588,6 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         MC_REQUIRE(h >= 2 && h <= t->k, "h must be in 2..k");
         MC_REQUIRE(!(t->skip_round && h >= t->k - 1), "not available on round-skipped levels");
         MC_REQUIRE(samples > 0, "samples must be > 0");
-        MC_REQUIRE(!t->stale && t->broken.empty(),
-                   "tables rebuilt since their totals were read: call mc_tables_status first");
         const ClassCatalog *cc = existing_catalogue(h);
         if (!cc)
             throw Error(MC_E_INVALID, "the graphlet catalogue of this size does not exist on this device yet "
@@ -1598,10 +1596,28 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         if (ncls > NOALLOC_MAX_CLASSES)
             throw Error(MC_E_UNSUPPORTED, "more graphlet classes than the static scratch holds (" +
                                               std::to_string(NOALLOC_MAX_CLASSES) + ")");
-        if (!t->prefix[h])
-            throw Error(MC_E_INVALID, "the root index of this level does not exist yet (creating it allocates); "
-                                      "call mc_total(h) first");
-        if (t->R[h] == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
+        // the level's root index, read under the lock that guards its
+        // publication; one made for an older colouring is refused, since
+        // remaking it allocates
+        const u128 *prefix = nullptr;
+        const uint32_t *bucket = nullptr;
+        u128 R = 0, D = 1;
+        {
+            std::lock_guard<std::mutex> lock(const_cast<mc_tables *>(t)->idx_mu);
+            MC_REQUIRE(!t->stale && t->broken.empty(),
+                       "tables rebuilt since their totals were read: call mc_tables_status first");
+            if (!t->prefix[h])
+                throw Error(MC_E_INVALID, "the root index of this level does not exist yet (creating it "
+                                          "allocates); call mc_total(h) first");
+            if (t->level_stale[h])
+                throw Error(MC_E_INVALID, "the root index of this level predates the last rebuild (remaking it "
+                                          "allocates); call mc_total(h) first");
+            prefix = t->prefix[h];
+            bucket = t->bucket[h];
+            R = t->R[h];
+            D = t->bucketD[h];
+        }
+        if (R == 0) throw Error(MC_E_INVALID, "no colourful treelet of size h");
         cudaStream_t s = (cudaStream_t)stream;
         NoAllocScratch *scr = noalloc_scratch();
         MC_CUDA(cudaMemsetAsync(scr->hist, 0, (size_t)ncls * sizeof(unsigned long long), s));
@@ -1615,10 +1631,10 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         for (int i = 0; i < cat.r[h]; ++i) {
             if (i < 64) a.allow0 |= 1ull << i; else a.allow1 |= 1ull << (i - 64);
         }
-        a.prefix = t->prefix[h];
-        a.R = t->R[h];
-        a.bucket = t->bucket[h];
-        a.D = t->bucketD[h];
+        a.prefix = prefix;
+        a.R = R;
+        a.bucket = bucket;
+        a.D = D;
         a.seed = seed;
         a.first_index = first_index;
         a.count = samples;
@@ -1629,7 +1645,7 @@ extern "C" mc_status mc_estimate_uniform_noalloc(const mc_tables *t, int h, uint
         launch_sampler(t, a, s);
         const double ip = inv_colourful_prob(t->k, h);
         MC_LAUNCH("estimate", s, uniform_estimate_kernel<<<(ncls + 127) / 128, 128, 0, s>>>(
-                                     scr->hist, scr->sigma, ncls, t->R[h] / (u128)t->copies_div(h), samples, ip, scr->est));
+                                     scr->hist, scr->sigma, ncls, R / (u128)t->copies_div(h), samples, ip, scr->est));
         int herr[2] = {0, 0};
         MC_CUDA(cudaMemcpyAsync(hits, scr->hist, (size_t)ncls * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         MC_CUDA(cudaMemcpyAsync(est, scr->est, (size_t)ncls * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -3,12 +3,14 @@
 //
 // Every slot is a host thread with its own CUDA stream.  Requests queue in
 // arrival order; the first queued request is admitted as soon as a slot is
-// idle and its device buffers fit the memory budget, so requests that
+// idle and its device buffers fit the free device memory (and the caller's
+// cap, if one was given), so requests that
 // arrive while others run start at once on another slot and their kernels
 // overlap on the device.  A request's results depend only on the tables,
 // its seed and its sample indices, so they are the same alone or in a mix.
 #include <chrono>
 #include <condition_variable>
+#include <algorithm>
 #include <deque>
 #include <map>
 #include <thread>
@@ -45,15 +47,57 @@ struct mc_server {
     int64_t next_id = 1;
     bool stop = false;
     std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;  // one per slot, created and checked at creation
+    ~mc_server()
+    {
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    }
 };
 
 namespace mc {
 
-// device bytes a request needs while it runs
-static size_t request_memory(const mc_request &r)
+int64_t bucket_count(int64_t n);
+
+// Device bytes a request allocates while it runs (outputs, scratch, and any
+// root or star index it creates on first use), from the request and the
+// tables it reads: what admission charges it.
+static size_t request_memory(const mc_tables *t, const mc_request &r)
 {
-    if (r.kind == MC_REQ_SAMPLE) return (size_t)r.count * ((size_t)r.h + 1) * 4 + (1 << 20);
-    return (size_t)4 << 20;  // estimates: histogram, class ids of one AGS batch, scratch
+    const int64_t n = t->g->n;
+    const size_t scan = (size_t)((n + 4095) / 4096 + 1) * 16;            // scan tile sums
+    const size_t index = (size_t)n * 16 + (size_t)(bucket_count(n) + 1) * 4 + scan + 64;  // prefix + buckets
+    const size_t small = 4096;                                            // flags, counters
+    if (r.kind == MC_REQ_SAMPLE) {
+        size_t m = (size_t)std::max<int64_t>(r.count, 1) * ((size_t)r.h + 1) * 4 + small;
+        if (r.unrooted_shape >= 0 || !t->prefix[r.h]) m += index;  // a shape's index is per call
+        return m;
+    }
+    const mc_estimate_params &p = r.est;
+    const int h = p.h;
+    const int ncls = mc_num_classes(h);
+    const size_t cls = (size_t)std::max(ncls, 1) * 8;
+    size_t m = small + 3 * cls;                                           // histogram, sigma, estimates
+    if (!t->prefix[h]) m += index;
+    if (p.mode == MC_EST_AGS) {
+        // a root index per treelet shape it samples from (at most all of
+        // them), one shape-total pass, and the class ids of one batch
+        const int nu = mc_num_unrooted(h);
+        const int64_t bmax = p.batch > 0 ? p.batch : (int64_t)1 << 22;
+        m += (size_t)std::max(nu, 1) * index + index + (size_t)bmax * 4;
+    }
+    if (p.star_samples > 0 && !t->g->star_prefix[h]) m += index + cls;
+    return m;
+}
+
+// Free device memory now (0 if the query fails).
+static size_t free_device_memory()
+{
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return free_b;
 }
 
 static void run_request(mc_server *sv, Request &q, cudaStream_t s)
@@ -85,21 +129,33 @@ static void run_request(mc_server *sv, Request &q, cudaStream_t s)
     }
 }
 
-static void worker(mc_server *sv)
+// Admission of the head of the queue: it fits the caller's cap (if any)
+// next to the running requests, and the device's free memory right now
+// still holds it on top of what the running requests were charged (they
+// may not have allocated it yet).  With nothing running it is admitted
+// regardless: a request larger than the device then fails alone with
+// MC_E_NOMEM.
+static bool admissible(const mc_server *sv, size_t mem)
+{
+    if (sv->in_use == 0) return true;
+    if (sv->budget && sv->in_use + mem > sv->budget) return false;
+    const size_t free_b = free_device_memory();
+    return free_b > sv->in_use && mem <= free_b - sv->in_use;
+}
+
+static void worker(mc_server *sv, cudaStream_t s)
 {
     cudaSetDevice(sv->device);
-    cudaStream_t s = nullptr;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (;;) {
         int64_t id = 0;
         {
             std::unique_lock<std::mutex> lock(sv->mu);
-            sv->cv.wait(lock, [&] {
-                if (sv->stop) return true;
-                if (sv->queue.empty()) return false;
-                const Request &head = sv->reqs.at(sv->queue.front());
-                return sv->in_use + head.mem <= sv->budget || sv->in_use == 0;
-            });
+            // memory freed by others (not only by this server) admits a
+            // waiting request at the next poll
+            while (!sv->stop) {
+                if (!sv->queue.empty() && admissible(sv, sv->reqs.at(sv->queue.front()).mem)) break;
+                sv->cv.wait_for(lock, std::chrono::milliseconds(2));
+            }
             if (sv->stop) break;
             id = sv->queue.front();
             sv->queue.pop_front();
@@ -124,7 +180,6 @@ static void worker(mc_server *sv)
         }
         sv->cv.notify_all();
     }
-    cudaStreamDestroy(s);
 }
 
 }  // namespace mc
@@ -144,13 +199,13 @@ extern "C" mc_status mc_server_create(const mc_tables *const *tables, int n_tabl
             sv->tables.push_back(tables[i]);
         }
         MC_CUDA(cudaGetDevice(&sv->device));
-        if (memory_budget == 0) {
-            size_t free_b = 0, total_b = 0;
-            MC_CUDA(cudaMemGetInfo(&free_b, &total_b));
-            memory_budget = free_b / 2;
-        }
         sv->budget = memory_budget;
-        for (int i = 0; i < slots; ++i) sv->workers.emplace_back(worker, sv);
+        for (int i = 0; i < slots; ++i) {
+            cudaStream_t s = nullptr;
+            MC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            sv->streams.push_back(s);
+        }
+        for (int i = 0; i < slots; ++i) sv->workers.emplace_back(worker, sv, sv->streams[i]);
     });
     if (st != MC_OK) {
         if (sv) {  // stop the workers started before the failure
@@ -180,11 +235,12 @@ extern "C" mc_status mc_server_submit(mc_server *sv, const mc_request *r, int64_
             MC_REQUIRE(r->kind == MC_REQ_ESTIMATE, "unknown request kind");
             MC_REQUIRE(r->est.h >= 2 && r->est.h <= t->k, "bad estimate request");
         }
+        const size_t mem = request_memory(t, *r);  // may build the class catalogue: outside the lock
         std::lock_guard<std::mutex> lock(sv->mu);
         const int64_t i = sv->next_id++;
         Request &q = sv->reqs[i];
         q.r = *r;
-        q.mem = request_memory(*r);
+        q.mem = mem;
         q.t_submit = Clock::now();
         sv->queue.push_back(i);
         *id = i;

@@ -99,7 +99,7 @@ def clique(n: int) -> CSRGraph:
 
 def lollipop(clique_size: int, tail: int) -> CSRGraph:
     """Clique on nodes 0..clique_size-1, plus a path of ``tail`` nodes
-    hanging off node clique_size-1 (the lower-bound graph of Section 4.2.2)."""
+    hanging off node clique_size-1 (the lower-bound graph of Section 4.3.2)."""
     a, b = np.triu_indices(clique_size, 1)
     t = np.arange(clique_size - 1, clique_size + tail - 1)
     src = np.concatenate([a, t])

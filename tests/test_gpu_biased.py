@@ -1,4 +1,4 @@
-"""Biased colouring (Section 3.4.3) and non-zero entry counts on the GPU
+"""Biased colouring (Section 3.5) and non-zero entry counts on the GPU
 against the oracle: colours bit for bit, tables and samples bit for bit,
 uniform and adaptive estimates with the biased colourful probability within
 2 ulp; non-zero counts equal those of the oracle's tables."""

@@ -12,7 +12,7 @@ e_{h-1} of v's per-colour neighbour counts.  An edge is colourful when its
 ends differ in colour, so the level-2 total is the number of bichromatic
 edges.  2000 samples of each size 5..7 must be colourful, connected, and
 carry the oracle's canonical class of their induced adjacency word.  10M
-adaptive samples (Section 3.3) must account for every hit.
+adaptive samples (Section 4.1) must account for every hit.
 """
 import os
 

@@ -1,4 +1,4 @@
-"""Pins for biased colouring (Section 3.4.3) in the oracle.
+"""Pins for biased colouring (Section 3.5) in the oracle.
 
 * Colour frequencies follow (1 - (k-1) lambda, lambda, ..., lambda) (chi-square);
   lambda = 0 is the uniform colouring.

@@ -1,5 +1,5 @@
 """Pins for the oracle's random numbers, colouring, graphlet classes and
-spanning-tree counts (Section 2.1, Section 4.3.3)."""
+spanning-tree counts (Section 2.1, Section 4.4.3)."""
 import itertools
 import math
 import random
