@@ -95,7 +95,7 @@ def _load():
                                             i64p, C.c_int64, i64p, C.c_uint32, f64p, u64p]
         lib.oc_estimate_ags.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                                         i64p, C.c_int, C.c_int64, i64p, i64p, C.c_uint32, f64p, u64p,
-                                        i64p]
+                                        i64p, C.c_int64, P, P, P]
         lib.oc_color_biased.argtypes = [C.c_int64, C.c_int, C.c_uint64, C.c_uint32, u8p]
         lib.oc_inv_colorful_prob.restype = C.c_double
         lib.oc_inv_colorful_prob.argtypes = [C.c_int, C.c_int, C.c_uint32]
@@ -321,17 +321,32 @@ class Tables:
         return est, hits
 
     def estimate_ags(self, h: int, seed: int, max_samples: int, cbar: int = 1000,
-                     first_index: int = 0, star_samples: int = 0, bias_q32: int = 0):
+                     first_index: int = 0, star_samples: int = 0, bias_q32: int = 0,
+                     trace: bool = False):
+        """(estimates, hits, stats).  trace=True adds to stats the first
+        treelet ("first") and, per switch, the treelet chosen ("trace_j"),
+        the samples drawn by then ("trace_at") and the weights w it was
+        chosen with ("trace_w", [switches, classes])."""
         _, s_ij = sigma(h)
         s_prime, s_star = self._skip_sigmas(h)
-        est = np.zeros(s_ij.shape[0], np.float64)
-        hits = np.zeros(s_ij.shape[0], np.uint64)
-        stats = np.zeros(3, np.int64)
+        ncls = s_ij.shape[0]
+        est = np.zeros(ncls, np.float64)
+        hits = np.zeros(ncls, np.uint64)
+        stats = np.zeros(4, np.int64)
+        cap = ncls if trace else 0
+        tj = np.zeros(max(cap, 1), np.int32)
+        tat = np.zeros(max(cap, 1), np.int64)
+        tw = np.zeros(max(cap * ncls, 1), np.float64)
         _check(_load().oc_estimate_ags(self._h, h, seed, first_index, max_samples, cbar,
                                        np.ascontiguousarray(s_ij), s_ij.shape[1], star_samples,
-                                       s_prime, s_star, bias_q32, est, hits, stats))
-        return est, hits, {"samples": int(stats[0]), "switches": int(stats[1]),
-                           "covered": int(stats[2])}
+                                       s_prime, s_star, bias_q32, est, hits, stats, cap,
+                                       tj.ctypes.data, tat.ctypes.data, tw.ctypes.data))
+        out = {"samples": int(stats[0]), "switches": int(stats[1]), "covered": int(stats[2])}
+        if trace:
+            ns = min(int(stats[1]), cap)
+            out.update(first=int(stats[3]), trace_j=tj[:ns].copy(), trace_at=tat[:ns].copy(),
+                       trace_w=tw[: ns * ncls].reshape(ns, ncls).copy())
+        return est, hits, out
 
 
 def ags_cbar(eps: float, delta: float, s: int) -> int:

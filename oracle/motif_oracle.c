@@ -1079,11 +1079,17 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
  *  - the result is est_i = (c_i / w_i) * (1/p), an estimate of the number
  *    of induced copies of H_i (c_i / w_i estimates its colourful copies);
  *    est_i = 0 when w_i = 0.
- * stats: [0] samples drawn, [1] switches, [2] graphlets covered. */
+ * stats: [0] samples drawn, [1] switches, [2] graphlets covered, [3] the
+ * first treelet (-1 if none).
+ * Trace (for tests; any pointer may be NULL): for the first trace_cap
+ * switches, trace_at[s] = samples drawn when switch s happened (the covering
+ * sample included), trace_j[s] = the treelet chosen, and trace_w[s * ncls +
+ * i] = the weight w_i it was chosen with. */
 int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_index, int64_t max_samples,
                     int64_t cbar, const int64_t *sigma_ij, int n_unrooted, int64_t n_star,
                     const int64_t *sigma_prime, const int64_t *sigma_star, uint32_t bias,
-                    double *est, uint64_t *hits, int64_t *stats)
+                    double *est, uint64_t *hits, int64_t *stats,
+                    int64_t trace_cap, int32_t *trace_j, int64_t *trace_at, double *trace_w)
 {
     if (h < 2 || level_missing(t, h) || max_samples < 0 || cbar < 1) return OC_INVALID;
     int st = ensure_classes(h);
@@ -1107,6 +1113,7 @@ int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
     int cur = -1;
     for (int j = 0; j < S; ++j)
         if (tj[j] > 0 && (cur < 0 || tj[j] > tj[cur])) cur = j;
+    stats[3] = cur;
     for (int i = 0; i < ncls; ++i) hits[i] = 0;
     int64_t drawn = 0, switches = 0, ncov = 0, target = ncls;
     if (t->skip_round && h == t->k) {      /* graphlets only stars span are left to the stars */
@@ -1146,6 +1153,12 @@ int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
                 if (best < 0 || val < bestv) { best = j; bestv = val; }
             }
             cur = best;
+            if (switches - 1 < trace_cap) {
+                if (trace_j) trace_j[switches - 1] = cur;
+                if (trace_at) trace_at[switches - 1] = drawn;
+                if (trace_w)
+                    for (int a = 0; a < ncls; ++a) trace_w[(size_t)(switches - 1) * ncls + a] = w[a];
+            }
         }
     }
 finish:
