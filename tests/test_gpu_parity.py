@@ -121,6 +121,30 @@ def test_zero_rooted_build(M, oracle, k, bits):
     assert np.array_equal(hits, ohits) and _ulp_close(est, oest)
 
 
+def test_k8_u128_with_hubs(M, oracle):
+    """k = 8 with u128 counts on a power-law graph whose hubs (33 nodes of
+    degree 65..140) take the chunked paths: the chunk-task gather, the hub
+    reduction, and the sampler's search over hub chunk prefix sums."""
+    g = synth.chung_lu(3000, 12000, 2.3, seed=11)
+    assert int(g.degrees().max()) > 64
+    k = 8
+    colors = oracle.color(g.n, k, 9)
+    G = M.Graph.from_csr(g)
+    T = M.Tables(G, M.color(G, k, 9), k, 128)
+    O = oracle.Tables(g, colors, k, 128)
+    assert_tables_equal(M, T, O, g, colors, k)
+    assert_totals_equal(T, O, k)
+    assert_samples_equal(T, O, k, seed=21, first=0, count=600)
+    assert_samples_equal(T, O, k, seed=22, first=987_654_321, count=200)
+    assert_samples_equal(T, O, 6, seed=23, first=0, count=300)   # h < k from the same tables
+    for j in (0, 5, 11, len(cat.unrooted_shapes(k)) - 1):
+        if T.total(k, j)[0] > 0:
+            assert_samples_equal(T, O, k, seed=24, first=0, count=100, unrooted=j)
+    est, hits, _ = T.estimate(k, seed=25, samples=2000)
+    oest, ohits = O.estimate_uniform(k, seed=25, n_samples=2000)
+    assert np.array_equal(hits, ohits) and _ulp_close(est, oest)
+
+
 def test_caller_colouring_and_device_csr(M, oracle):
     import torch
     g = synth.chung_lu(3000, 20000, 2.5, seed=9)

@@ -33,6 +33,7 @@ CASES = [
     (lambda: synth.chung_lu(5000, 30000, 2.3, seed=2), 6, 128, 4),
     (lambda: synth.chung_lu(3000, 15000, 2.4, seed=7), 7, 128, 5),
     (lambda: synth.erdos_renyi(300, 6.0, seed=6), 8, 128, 6),
+    (lambda: synth.chung_lu(3000, 12000, 2.3, seed=11), 8, 128, 9),  # k = 8 with hubs (degree <= 140)
 ]
 
 
