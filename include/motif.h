@@ -182,11 +182,12 @@ mc_status mc_tables_status(const mc_tables *t, void *stream);
 
 /* Layout of the level-h table (which = 0: counts c, h = 1..k; which = 1:
  * neighbour sums S, h = 1..k-1).  Row v holds row_entries entries of
- * entry_bytes (8 or 16, little-endian, low word first).  Entry
- * (s, rho) sits at s * B + rho, s the rooted shape id, B = C(k-1, h-1) for
- * c and C(k-1, h) for S, and rho the colex rank of the colour set without c_v
- * after deleting colour c_v from the palette (colours above c_v move down by
- * one).  Only sets that contain c_v (for c) or avoid it (for S) are stored. */
+ * entry_bytes (8 or 16, little-endian, low word first).  Rows are
+ * set-major: entry (rho, s) sits at rho * r_h + s, s the rooted shape id,
+ * r_h = mc_num_shapes(h), and rho the colex rank (among C(k-1, h-1) sets for
+ * c, C(k-1, h) for S) of the colour set without c_v after deleting colour
+ * c_v from the palette (colours above c_v move down by one).  Only sets that
+ * contain c_v (for c) or avoid it (for S) are stored. */
 mc_status mc_table_layout(const mc_tables *t, int h, int which, int64_t *row_entries,
                           int *entry_bytes);
 /* Non-zero entries of a level (which = 0: c, which = 1: S), counted on the

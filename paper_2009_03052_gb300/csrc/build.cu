@@ -19,22 +19,29 @@ namespace mc {
 enum : int { ERR_OVERFLOW = 1, ERR_INEXACT = 2, ERR_COLOUR = 4, ERR_SEARCH = 8 };
 
 // ---------------------------------------------------------------------------
-// level 1: S_1(v)[{a}] = number of neighbours of colour a != c_v
-// (c(single node, {c_u}, u) = 1).  One warp per node; one ballot per colour.
-// ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// level h >= 2 neighbour sums.  One warp per task; a task is a node (all its
-// neighbours) or a chunk of HUB_CHUNK neighbours of a hub, whose partial row
-// goes to `partial`.  The warp splits into 32/G groups of G lanes; a group
-// takes one neighbour at a time, its lanes the S entries (lane j owns
-// entries j, j+G, ...).  The colour-relative index map for (c_v, c_u) lives
-// in shared memory.
+// Neighbour sums of level h >= 2 (the inner sum over u of Eq. 1):
+//   S_h(v)[rho'', s] = sum_{u ~ v} c_h(u)[map(c_v, c_u, rho''), s].
+// Rows are set-major, so the entries of one colour set (all r_h shapes) are
+// contiguous, and a neighbour u contributes whole sets: the S sets holding
+// c_u take u's sets that avoid c_v.  A row is handled in units of UB bytes
+// (16 when a set's bytes are a multiple of 16, else 8); a lane owns S units
+// j, j + G, ... of its node and, per neighbour, loads the one source unit
+// that feeds each (map in shared memory), U neighbours in flight.
+//   * nodes of degree <= HUB_CHUNK: G lanes per node, 32 / G nodes per warp,
+//     taken in the order `order` (descending degree, so the nodes of a warp
+//     have nearly equal degrees);
+//   * hub chunks (HUB_CHUNK consecutive neighbours of a hub): a warp per
+//     chunk, its 32 / G groups on different neighbours, summed by shuffles;
+//     the partial row goes to `partial`, entry-major per hub.
+// The first `chunk_blocks` blocks take the hub chunks, the rest the nodes.
 // ---------------------------------------------------------------------------
 struct GatherArgs {
     const int64_t *row_ptr;
     const uint32_t *col;
     const uint8_t *colors;
     const uint8_t *ecol;
+    const uint4 *sched;      // nodes of degree <= HUB_CHUNK, descending degree: (v, e0 lo, e0 hi, degree)
+    int64_t n_small;
     const int32_t *node_chunk0;
     const void *src;   // c_h, n x Wc
     void *dst;         // S_h, n x Ws
@@ -43,11 +50,67 @@ struct GatherArgs {
     const int64_t *chunk_e0, *chunk_e1;
     const int16_t *gmap;
     int64_t n, n_chunks;
-    int k, Bc, Bs, Wc, Ws;
+    int k, Bs, Wc, Ws;
+    int ups;           // units per colour set
+    int wc_units, ws_units;
+    int chunk_blocks;
     int *err;
 };
 
-template <typename CT, int G, int MAXE>
+// A unit of UB bytes of a row of CT counts, with exact (overflow-checked) adds.
+template <typename CT, int UB> struct Unit;
+template <> struct Unit<uint64_t, 8> {
+    uint64_t a;
+    __device__ __forceinline__ void zero() { a = 0; }
+    __device__ __forceinline__ void load(const void *p) { a = __ldg((const unsigned long long *)p); }
+    __device__ __forceinline__ bool add(const Unit &x) { return add_ovf(a, x.a); }
+    __device__ __forceinline__ void store(void *p) const { *(uint64_t *)p = a; }
+    __device__ __forceinline__ Unit xor_shfl(int d) const { Unit r; r.a = __shfl_xor_sync(0xffffffffu, a, d); return r; }
+    __device__ __forceinline__ uint64_t entry(int i) const { return a; }
+};
+template <> struct Unit<uint64_t, 16> {
+    uint64_t a, b;
+    __device__ __forceinline__ void zero() { a = b = 0; }
+    __device__ __forceinline__ void load(const void *p)
+    {
+        const ulonglong2 v = __ldg((const ulonglong2 *)p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ __forceinline__ bool add(const Unit &x)
+    {
+        const bool o1 = add_ovf(a, x.a);
+        const bool o2 = add_ovf(b, x.b);
+        return o1 | o2;
+    }
+    __device__ __forceinline__ void store(void *p) const { *(ulonglong2 *)p = make_ulonglong2(a, b); }
+    __device__ __forceinline__ Unit xor_shfl(int d) const
+    {
+        Unit r;
+        r.a = __shfl_xor_sync(0xffffffffu, a, d);
+        r.b = __shfl_xor_sync(0xffffffffu, b, d);
+        return r;
+    }
+    __device__ __forceinline__ uint64_t entry(int i) const { return i ? b : a; }
+};
+template <> struct Unit<u128, 16> {
+    u128 a;
+    __device__ __forceinline__ void zero() { a = 0; }
+    __device__ __forceinline__ void load(const void *p)
+    {
+        const ulonglong2 v = __ldg((const ulonglong2 *)p);
+        a = ((u128)v.y << 64) | v.x;
+    }
+    __device__ __forceinline__ bool add(const Unit &x) { return add_ovf(a, x.a); }
+    __device__ __forceinline__ void store(void *p) const
+    {
+        *(ulonglong2 *)p = make_ulonglong2((uint64_t)a, (uint64_t)(a >> 64));
+    }
+    __device__ __forceinline__ Unit xor_shfl(int d) const { Unit r; r.a = shfl_xor(a, d); return r; }
+    __device__ __forceinline__ u128 entry(int i) const { return a; }
+};
+
+template <typename CT, int UB, int G, int NU, int U>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a)
 {
     extern __shared__ int16_t s_map[];
@@ -55,116 +118,190 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
     for (int i = threadIdx.x; i < mapn; i += blockDim.x) s_map[i] = a.gmap[i];
     __syncthreads();
 
+    typedef Unit<CT, UB> UT;
+    constexpr int NG = 32 / G;
+    constexpr int EPU = UB / (int)sizeof(CT);  // entries per unit
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, j = lane % G;
-    constexpr int NG = 32 / G;
-    int rowoff[MAXE], rho[MAXE];
-    bool own[MAXE];
+    // the lane's units: set and unit within the set
+    int uset[NU], usub[NU];
+    bool own[NU];
 #pragma unroll
-    for (int i = 0; i < MAXE; ++i) {
-        const int e = j + i * G;
-        own[i] = e < a.Ws;
-        const int s = e / a.Bs;
-        rho[i] = own[i] ? e - s * a.Bs : 0;
-        rowoff[i] = own[i] ? s * a.Bc : 0;
+    for (int i = 0; i < NU; ++i) {
+        const int un = j + i * G;
+        own[i] = un < a.ws_units;
+        uset[i] = own[i] ? un / a.ups : 0;
+        usub[i] = own[i] ? un - uset[i] * a.ups : 0;
     }
-    const CT *__restrict__ src = (const CT *)a.src;
-    const int64_t ntasks = a.n_chunks + a.n;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const char *__restrict__ src = (const char *)a.src;
+    const int64_t rowb = (int64_t)a.wc_units * UB;
+    const int wpb = blockDim.x >> 5;
     bool ovf = false;
-    for (int64_t t = warp; t < ntasks; t += nwarps) {
-        int64_t v, e0, e1;
-        CT *out;
-        int64_t ostride = 1;
-        if (t < a.n_chunks) {
-            // partial row of one hub chunk, stored entry-major per hub:
-            // [first chunk * Ws + entry * (chunks of the hub) + chunk]
-            v = a.chunk_node[t];
-            e0 = a.chunk_e0[t];
-            e1 = a.chunk_e1[t];
-            const int64_t c0 = a.node_chunk0[v];
-            ostride = (a.row_ptr[v + 1] - a.row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
-            out = (CT *)a.partial + c0 * a.Ws + (t - c0);
-        } else {
-            v = t - a.n_chunks;
-            e0 = a.row_ptr[v];
-            e1 = a.row_ptr[v + 1];
-            if (e1 - e0 > HUB_CHUNK) continue;  // done by its chunks
-            out = (CT *)a.dst + v * a.Ws;
-        }
-        const int cv = a.colors[v];
-        CT acc[MAXE];
+    UT acc[NU];
+
+    if ((int)blockIdx.x < a.chunk_blocks) {
+        // ---- hub chunks: a warp per chunk
+        for (int64_t t = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < a.n_chunks;
+             t += (int64_t)a.chunk_blocks * wpb) {
+            const int64_t v = a.chunk_node[t];
+            const int64_t e0 = a.chunk_e0[t], e1 = a.chunk_e1[t];
+            const int cv = a.colors[v];
 #pragma unroll
-        for (int i = 0; i < MAXE; ++i) acc[i] = 0;
-        // 32 neighbours at a time: one coalesced load of their ids and
-        // colours, handed to the groups by shuffles; each group takes U of
-        // them per round so that U rows are in flight at once
-        constexpr int U = G < 4 ? G : 4;
-        for (int64_t b = e0; b < e1; b += 32) {
-            const int64_t e = b + lane;
-            const bool in = e < e1;
-            const uint32_t my_u = in ? a.col[e] : 0u;
-            const int my_cu = in ? (int)a.ecol[e] : cv;
-            const int nb = (int)min((int64_t)32, e1 - b);
-            const int rounds = (nb + NG * U - 1) / (NG * U);
-            for (int r = 0; r < rounds; ++r) {
+            for (int i = 0; i < NU; ++i) acc[i].zero();
+            for (int64_t b = e0; b < e1; b += NG * U) {
+                UT x[U][NU];
 #pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                    const int idx = r * NG * U + uu * NG + grp;
-                    const uint32_t u = __shfl_sync(0xffffffffu, my_u, idx & 31);
-                    const int cu = __shfl_sync(0xffffffffu, my_cu, idx & 31);
-                    // a neighbour of colour c_v adds nothing: every set holding
-                    // c_u then holds c_v
-                    if (idx < nb && cu != cv) {
-                        const CT *row = src + (int64_t)u * a.Wc;
-                        const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
+                for (int q = 0; q < U; ++q) {
+                    const int64_t e = b + q * NG + grp;
+                    const bool in = e < e1;
+                    const uint32_t u = in ? a.col[e] : 0u;
+                    const int cu = in ? (int)a.ecol[e] : cv;
+                    const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
 #pragma unroll
-                        for (int i = 0; i < MAXE; ++i) {
-                            if (own[i]) {
-                                const int sidx = gm[rho[i]];
-                                if (sidx >= 0) ovf |= add_ovf(acc[i], row[rowoff[i] + sidx]);
-                            }
-                        }
+                    for (int i = 0; i < NU; ++i) {
+                        const int ss = (in && cu != cv && own[i]) ? gm[uset[i]] : -1;
+                        if (ss >= 0) x[q][i].load(src + (int64_t)u * rowb + (int64_t)(ss * a.ups + usub[i]) * UB);
+                        else x[q][i].zero();
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < U; ++q)
+#pragma unroll
+                    for (int i = 0; i < NU; ++i) ovf |= acc[i].add(x[q][i]);
+            }
+#pragma unroll
+            for (int d = G; d < 32; d <<= 1)
+#pragma unroll
+                for (int i = 0; i < NU; ++i) ovf |= acc[i].add(acc[i].xor_shfl(d));
+            if (grp == 0) {
+                // partial row of the chunk, entry-major per hub:
+                // [first chunk * Ws + entry * (chunks of the hub) + chunk]
+                const int64_t c0 = a.node_chunk0[v];
+                const int64_t nch = (a.row_ptr[v + 1] - a.row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
+                CT *out = (CT *)a.partial + c0 * a.Ws + (t - c0);
+#pragma unroll
+                for (int i = 0; i < NU; ++i)
+                    if (own[i])
+#pragma unroll
+                        for (int w = 0; w < EPU; ++w)
+                            out[(int64_t)((j + i * G) * EPU + w) * nch] = acc[i].entry(w);
             }
         }
+        if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+        return;
+    }
+
+    // ---- nodes of degree <= HUB_CHUNK: G lanes per node.  The ids and
+    // colours of the next U neighbours are loaded while the rows of the
+    // current U are in flight.
+    const int64_t nblk = (int64_t)gridDim.x - a.chunk_blocks;
+    const int64_t warp0 = ((int64_t)blockIdx.x - a.chunk_blocks) * wpb + (threadIdx.x >> 5);
+    for (int64_t base = warp0 * NG; base < a.n_small; base += nblk * wpb * NG) {
+        const int64_t idx = base + grp;
+        const bool valid = idx < a.n_small;
+        const uint4 rec = valid ? a.sched[idx] : make_uint4(0u, 0u, 0u, 0u);
+        const int64_t v = rec.x;
+        const int64_t e0 = (int64_t)(((uint64_t)rec.z << 32) | rec.y);
+        const int d = (int)rec.w;
+        const int cv = valid ? (int)a.colors[v] : 0;
+        const int dmax = __reduce_max_sync(0xffffffffu, (unsigned)d);
 #pragma unroll
-        for (int d = G; d < 32; d <<= 1)
+        for (int i = 0; i < NU; ++i) acc[i].zero();
+        uint32_t nu_[U];
+        int ncu[U];
 #pragma unroll
-            for (int i = 0; i < MAXE; ++i) {
-                const CT o = shfl_xor(acc[i], d);
-                ovf |= add_ovf(acc[i], o);
+        for (int q = 0; q < U; ++q) {
+            const bool in = q < d;
+            nu_[q] = in ? a.col[e0 + q] : 0u;
+            ncu[q] = in ? (int)a.ecol[e0 + q] : cv;
+        }
+        for (int off = 0; off < dmax; off += U) {
+            uint32_t u[U];
+            int cu[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) { u[q] = nu_[q]; cu[q] = ncu[q]; }
+            UT x[U][NU];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int16_t *gm = s_map + (cv * a.k + cu[q]) * a.Bs;
+#pragma unroll
+                for (int i = 0; i < NU; ++i) {
+                    const int ss = (cu[q] != cv && own[i]) ? gm[uset[i]] : -1;
+                    if (ss >= 0) x[q][i].load(src + (int64_t)u[q] * rowb + (int64_t)(ss * a.ups + usub[i]) * UB);
+                    else x[q][i].zero();
+                }
             }
-        if (grp == 0) {
+            if (off + U < dmax) {
 #pragma unroll
-            for (int i = 0; i < MAXE; ++i)
-                if (own[i]) out[(j + i * G) * ostride] = acc[i];
+                for (int q = 0; q < U; ++q) {
+                    const bool in = off + U + q < d;
+                    nu_[q] = in ? a.col[e0 + off + U + q] : 0u;
+                    ncu[q] = in ? (int)a.ecol[e0 + off + U + q] : cv;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q)
+#pragma unroll
+                for (int i = 0; i < NU; ++i) ovf |= acc[i].add(x[q][i]);
+        }
+        if (valid) {
+            char *out = (char *)a.dst + v * (int64_t)a.ws_units * UB;
+#pragma unroll
+            for (int i = 0; i < NU; ++i)
+                if (own[i]) acc[i].store(out + (int64_t)(j + i * G) * UB);
         }
     }
     if (ovf) atomicOr(a.err, ERR_OVERFLOW);
 }
 
-// Sum the chunk partials of each hub into its S row.
+// Sum the chunk partials of each hub into its S row.  The chunk sums of a
+// (hub, S entry) pair are contiguous; they become their inclusive prefix
+// (the sampler binary-searches it) and the last prefix is the hub's
+// neighbour sum.  Any overflowing partial sum means the total overflows too.
+// Hubs of at most HUB_SERIAL chunks: a thread per (hub, entry) scans them in
+// order (the threads of a warp take consecutive entries of one hub, whose
+// chunk sums are adjacent); larger hubs: a warp per (hub, entry), 32 chunks
+// per warp scan.
+
+template <typename CT>
+__global__ void hub_reduce_small_kernel(CT *__restrict__ partial, CT *__restrict__ dst,
+                                        const uint32_t *__restrict__ hub_node,
+                                        const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int Ws, int *err)
+{
+    bool ovf = false;
+    const int64_t total = n_hubs * Ws;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t hub = i / Ws;
+        const int e = (int)(i - hub * Ws);
+        const int64_t c0 = hub_chunk0[hub], nch = hub_chunk0[hub + 1] - c0;
+        if (nch > HUB_SERIAL) continue;
+        CT *p = partial + c0 * Ws + e * nch;
+        CT run = 0;
+        for (int64_t c = 0; c < nch; ++c) {
+            ovf |= add_ovf(run, p[c]);
+            p[c] = run;
+        }
+        dst[(int64_t)hub_node[hub] * Ws + e] = run;
+    }
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
 template <typename CT>
 __global__ void hub_reduce_kernel(CT *__restrict__ partial, CT *__restrict__ dst,
                                   const uint32_t *__restrict__ hub_node,
-                                  const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, int Ws,
-                                  int *err)
+                                  const int64_t *__restrict__ hub_chunk0, const uint32_t *__restrict__ big_hub,
+                                  int64_t n_big, int Ws, int *err)
 {
-    // a warp per (hub, S entry): the chunk sums, contiguous for the pair,
-    // become their inclusive prefix (the sampler binary-searches it) by warp
-    // scans of 32 chunks at a time; the last prefix is the hub's neighbour
-    // sum.  Any overflowing partial sum means the total overflows too.
     bool ovf = false;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t total = n_hubs * Ws;
+    const int64_t total = n_big * Ws;
     for (int64_t i = warp; i < total; i += nwarps) {
-        const int64_t hub = i / Ws;
-        const int e = (int)(i - hub * Ws);
+        const int64_t bi = i / Ws;
+        const int e = (int)(i - bi * Ws);
+        const int64_t hub = big_hub[bi];
         const int64_t c0 = hub_chunk0[hub], nch = hub_chunk0[hub + 1] - c0;
         CT *p = partial + c0 * Ws + e * nch;
         CT carry = 0;
@@ -200,7 +337,7 @@ struct MergeArgs {
     const uint32_t *terms;
     void *out;
     int64_t n;
-    int W;
+    int W, Bc, R;                     // row width, colour sets and shapes of the level
     const uint8_t *zero_root_colors;  // set: only colour-0 nodes get counts
     int *err;
 };
@@ -212,11 +349,16 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
     const int64_t total = a.n * a.W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        // node and output entry; 32-bit division when the level fits 2^32 entries
+        // node and output entry; 32-bit division when the level fits 2^32
+        // entries.  Threads walk a row in (shape, set) order, so the threads
+        // of a warp mostly share one shape and one program length, and write
+        // entry (set, shape) at its set-major position.
         const int64_t v = total <= 0xffffffffll ? (int64_t)((uint32_t)t / (uint32_t)a.W) : t / a.W;
-        const int o = (int)(t - v * a.W);
+        const int q = (int)(t - v * a.W);
+        const int sh = q / a.Bc;
+        const int o = (q - sh * a.Bc) * a.R + sh;
         if (a.zero_root_colors && a.zero_root_colors[v] != 0) {
-            ((CT *)a.out)[t] = 0;
+            ((CT *)a.out)[v * a.W + o] = 0;
             continue;
         }
         const int info = a.info[o];
@@ -235,9 +377,9 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
                 ovf |= add_ovf(sum, p);
             }
         }
-        CT q;
-        if (!exact_div(sum, a.div[beta], q)) inexact = true;
-        ((CT *)a.out)[t] = q;
+        CT qt;
+        if (!exact_div(sum, a.div[beta], qt)) inexact = true;
+        ((CT *)a.out)[v * a.W + o] = qt;
     }
     if (ovf) atomicOr(a.err, ERR_OVERFLOW);
     if (inexact) atomicOr(a.err, ERR_INEXACT);
@@ -249,7 +391,7 @@ __global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ Merg
 // nodes for the root draw).
 // ---------------------------------------------------------------------------
 template <typename CT, int G>
-__global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ c, int64_t n, int W, int Bc,
+__global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ c, int64_t n, int W, int R,
                                                          uint64_t allow0, uint64_t allow1,
                                                          u128 *__restrict__ tot, int *err)
 {
@@ -265,7 +407,7 @@ __global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ 
         u128 s = 0;
         if (v < n)
             for (int e = j; e < W; e += G) {
-                const int sh = e / Bc;
+                const int sh = e % R;  // set-major row: entry e is (set e / R, shape e % R)
                 const bool ok = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
                 if (ok) ovf |= add_ovf(s, widen(c[v * W + e]));
             }
@@ -634,19 +776,19 @@ ExactDiv make_div(int beta)
 template <typename CT> size_t bytes_of() { return sizeof(CT); }
 
 template <typename CT>
-static void launch_row_totals_t(const CT *c, int64_t n, int W, int Bc, uint64_t allow0, uint64_t allow1, u128 *tot,
+static void launch_row_totals_t(const CT *c, int64_t n, int W, int R, uint64_t allow0, uint64_t allow1, u128 *tot,
                                 int *err, cudaStream_t s)
 {
     int G = 1;
     while (G < W && G < 32) G <<= 1;
     const int grid = grid_for((n * G + 31) / 32 * 32, 256);
     switch (G) {
-    case 1: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 1><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
-    case 2: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 2><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
-    case 4: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 4><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
-    case 8: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 8><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
-    case 16: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 16><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
-    default: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 32><<<grid, 256, 0, s>>>(c, n, W, Bc, allow0, allow1, tot, err)); break;
+    case 1: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 1><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
+    case 2: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 2><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
+    case 4: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 4><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
+    case 8: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 8><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
+    case 16: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 16><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
+    default: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 32><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
     }
 }
 
@@ -655,11 +797,11 @@ void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allo
 {
     const int64_t n = t->g->n;
     if (n == 0) return;
-    const int W = t->geo.Wc[h], Bc = t->geo.Bc[h];
+    const int W = t->geo.Wc[h], R = shape_catalog().r[h];
     if (t->bits == 64)
-        launch_row_totals_t<uint64_t>((const uint64_t *)t->c[h], n, W, Bc, allow0, allow1, tot, err, s);
+        launch_row_totals_t<uint64_t>((const uint64_t *)t->c[h], n, W, R, allow0, allow1, tot, err, s);
     else
-        launch_row_totals_t<u128>((const u128 *)t->c[h], n, W, Bc, allow0, allow1, tot, err, s);
+        launch_row_totals_t<u128>((const u128 *)t->c[h], n, W, R, allow0, allow1, tot, err, s);
 }
 
 static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gather_h2", "gather_h3",
@@ -668,20 +810,59 @@ static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gat
 static const char *const kMergeName[MAXK + 1] = {"merge_h0", "merge_h1", "merge_h2", "merge_h3", "merge_h4",
                                                  "merge_h5", "merge_h6", "merge_h7", "merge_h8"};
 
-template <typename CT> static void launch_gather(const GatherArgs &ga, int G, int h, cudaStream_t s)
+// Instantiations of the gather: G lanes per node (a power of two covering
+// the S row's units, at most 32), NU units per lane when a row has more than
+// 32 units, and U neighbours in flight (fewer when each lane owns many units).
+template <typename CT, int UB, int G, int NU>
+static void launch_gather_g(const GatherArgs &ga, int grid, size_t smem, const char *nm, cudaStream_t s)
+{
+    constexpr int U = NU >= 16 ? 1 : NU >= 8 ? 2 : NU >= 4 ? 4 : 8;
+    MC_LAUNCH(nm, s, gather_kernel<CT, UB, G, NU, U><<<grid, 256, smem, s>>>(ga));
+}
+
+template <typename CT, int UB>
+static void launch_gather_ub(const GatherArgs &ga, int h, cudaStream_t s)
 {
     const char *nm = kGatherName[h];
-    const int64_t ntasks = ga.n_chunks + ga.n;
-    const int grid = grid_for(ntasks * 32, 256);
+    int G = 1;
+    while (G < ga.ws_units && G < 32) G <<= 1;
+    int NU = 1;
+    while (NU * 32 < ga.ws_units) NU <<= 1;
+    if (NU > 16) throw Error(MC_E_INTERNAL, "gather: S row too wide");
+    const int NG = 32 / G;
+    const int wpb = 256 / 32;
+    GatherArgs g2 = ga;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    g2.chunk_blocks = (int)std::min<int64_t>((ga.n_chunks + wpb - 1) / wpb, cap);
+    const int64_t node_blocks = std::max<int64_t>(1, std::min<int64_t>((ga.n_small + NG * wpb - 1) / (NG * wpb), cap));
+    const int grid = (int)(g2.chunk_blocks + node_blocks);
     const size_t smem = (size_t)ga.k * ga.k * ga.Bs * sizeof(int16_t);
     switch (G) {
-    case 1: MC_LAUNCH(nm, s, gather_kernel<CT, 1, 1><<<grid, 256, smem, s>>>(ga)); break;
-    case 2: MC_LAUNCH(nm, s, gather_kernel<CT, 2, 1><<<grid, 256, smem, s>>>(ga)); break;
-    case 4: MC_LAUNCH(nm, s, gather_kernel<CT, 4, 1><<<grid, 256, smem, s>>>(ga)); break;
-    case 8: MC_LAUNCH(nm, s, gather_kernel<CT, 8, 1><<<grid, 256, smem, s>>>(ga)); break;
-    case 16: MC_LAUNCH(nm, s, gather_kernel<CT, 16, 1><<<grid, 256, smem, s>>>(ga)); break;
-    default: MC_LAUNCH(nm, s, gather_kernel<CT, 32, 6><<<grid, 256, smem, s>>>(ga)); break;
+    case 1: launch_gather_g<CT, UB, 1, 1>(g2, grid, smem, nm, s); break;
+    case 2: launch_gather_g<CT, UB, 2, 1>(g2, grid, smem, nm, s); break;
+    case 4: launch_gather_g<CT, UB, 4, 1>(g2, grid, smem, nm, s); break;
+    case 8: launch_gather_g<CT, UB, 8, 1>(g2, grid, smem, nm, s); break;
+    case 16: launch_gather_g<CT, UB, 16, 1>(g2, grid, smem, nm, s); break;
+    default:
+        switch (NU) {
+        case 1: launch_gather_g<CT, UB, 32, 1>(g2, grid, smem, nm, s); break;
+        case 2: launch_gather_g<CT, UB, 32, 2>(g2, grid, smem, nm, s); break;
+        case 4: launch_gather_g<CT, UB, 32, 4>(g2, grid, smem, nm, s); break;
+        case 8: launch_gather_g<CT, UB, 32, 8>(g2, grid, smem, nm, s); break;
+        default: launch_gather_g<CT, UB, 32, 16>(g2, grid, smem, nm, s); break;
+        }
     }
+}
+
+template <typename CT> static void launch_gather(GatherArgs &ga, const mc_graph *g, int r, int h, cudaStream_t s)
+{
+    const int B = (int)sizeof(CT);
+    const int UB = (r * B) % 16 == 0 ? 16 : 8;  // a unit never straddles two colour sets
+    ga.ups = r * B / UB;
+    ga.wc_units = ga.Wc * B / UB;
+    ga.ws_units = ga.Ws * B / UB;
+    if (UB == 16) launch_gather_ub<CT, 16>(ga, h, s);
+    else launch_gather_ub<uint64_t, 8>(ga, h, s);
 }
 
 template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStream_t s)
@@ -724,6 +905,8 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
         ma.terms = t->m_terms[h];
         ma.out = t->c[h];
         ma.W = G.Wc[h];
+        ma.Bc = G.Bc[h];
+        ma.R = shape_catalog().r[h];
         ma.zero_root_colors = (t->zero_root && h == k) ? t->colors : nullptr;
         MC_LAUNCH(kMergeName[h], s, merge_kernel<CT><<<grid_for(n * G.Wc[h], 256), 256, 0, s>>>(ma));
         if (h <= k - 1) {
@@ -743,17 +926,20 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
             ga.n = n;
             ga.n_chunks = g->n_chunks;
             ga.k = k;
-            ga.Bc = G.Bc[h];
             ga.Bs = G.Bs[h];
             ga.Wc = G.Wc[h];
             ga.Ws = G.Ws[h];
             ga.err = err;
-            int grp = 1;
-            while (grp < G.Ws[h] && grp < 32) grp <<= 1;
-            launch_gather<CT>(ga, grp, h, s);
+            ga.sched = g->sched;
+            ga.n_small = g->n_small;
+            launch_gather<CT>(ga, g, shape_catalog().r[h], h, s);
             if (g->n_hubs) {
-                MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h] * 32, 256), 256, 0, s>>>(
+                MC_LAUNCH("hub_reduce", s, hub_reduce_small_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
                     (CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
+                if (g->n_big_hubs)
+                    MC_LAUNCH("hub_reduce", s, hub_reduce_kernel<CT><<<grid_for(g->n_big_hubs * G.Ws[h] * 32, 256), 256, 0, s>>>(
+                        (CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->big_hub, g->n_big_hubs,
+                        G.Ws[h], err));
             }
         }
     }

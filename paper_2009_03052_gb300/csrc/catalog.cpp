@@ -238,35 +238,35 @@ static Programs build_programs(int k, bool skip)
             P.copies[j] = a;
         }
     }
+    // outputs in row order: set-major, o = rho * r_h + s (every shape of
+    // one colour set side by side)
     for (int h = 2; h <= k; ++h) {
         if (skip && h == k - 1) continue;
         MergeLevel &M = P.merge[h];
-        for (int s = 0; s < cat.r[h]; ++s) {
-            const Shape &T = cat.shapes[cat.gid(h, s)];
-            int left = T.left, right = T.right, beta = T.beta;
-            if (skip && h == k) {
-                left = P.bal_left[cat.gid(h, s)], right = P.bal_right[cat.gid(h, s)], beta = P.bal_beta[cat.gid(h, s)];
-                if (left < 0) {  // not counted: no terms
-                    for (int rho = 0; rho < G.Bc[h]; ++rho) {
+        for (int rho = 0; rho < G.Bc[h]; ++rho) {
+            // D: the h-1 colours of C other than c_v, as a relative set
+            const unsigned D = colex_unrank(h - 1, rho);
+            for (int s = 0; s < cat.r[h]; ++s) {
+                const Shape &T = cat.shapes[cat.gid(h, s)];
+                int left = T.left, right = T.right, beta = T.beta;
+                if (skip && h == k) {
+                    left = P.bal_left[cat.gid(h, s)], right = P.bal_right[cat.gid(h, s)], beta = P.bal_beta[cat.gid(h, s)];
+                    if (left < 0) {  // not counted: no terms
                         M.offset.push_back((int32_t)M.terms.size());
                         M.info.push_back(1 | (1 << 4) | (1 << 8));
+                        continue;
                     }
-                    continue;
                 }
-            }
-            const Shape &A = cat.shapes[left];
-            const Shape &B = cat.shapes[right];
-            const int h1 = A.size, h2 = B.size;
-            for (int rho = 0; rho < G.Bc[h]; ++rho) {
-                // D: the h-1 colours of C other than c_v, as a relative set
-                const unsigned D = colex_unrank(h - 1, rho);
+                const Shape &A = cat.shapes[left];
+                const Shape &B = cat.shapes[right];
+                const int h1 = A.size, h2 = B.size;
                 M.offset.push_back((int32_t)M.terms.size());
                 int nterms = 0;
                 for (unsigned sub = D;; sub = (sub - 1) & D) {  // D'' subset of D
                     if (__builtin_popcount(sub) == h2) {
                         const unsigned Dp = D & ~sub;        // D' = D \ D''
-                        const int ia = h1 == 1 ? 0 : A.local * G.Bc[h1] + colex_rank(Dp);
-                        const int ib = B.local * G.Bs[h2] + colex_rank(sub);
+                        const int ia = h1 == 1 ? 0 : colex_rank(Dp) * cat.r[h1] + A.local;
+                        const int ib = colex_rank(sub) * cat.r[h2] + B.local;
                         M.terms.push_back((uint32_t)ia | ((uint32_t)ib << 16));
                         ++nterms;
                     }

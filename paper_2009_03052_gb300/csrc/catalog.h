@@ -50,18 +50,20 @@ struct Geometry {
 };
 Geometry make_geometry(int k);
 
-// Merge program of level h: for output entry o = (shape s, colour set rho)
-// the list of (index into the c_{|T'|} row, index into the S_{|T''|} row)
-// pairs of Eq. (1), one per split of the colour set.
+// Rows are set-major: entry (colour set rho, shape s) of a level-h row sits
+// at rho * r_h + s, so the entries of one colour set are contiguous.
+// Merge program of level h: for output entry o = rho * r_h + s the list of
+// (index into the c_{|T'|} row, index into the S_{|T''|} row) pairs of
+// Eq. (1), one per split of the colour set.
 struct MergeLevel {
     std::vector<int32_t> info;    // per output: h1 | h2 << 4 | beta << 8 | nterms << 16
     std::vector<int32_t> offset;  // per output: first term
     std::vector<uint32_t> terms;  // ia | ib << 16
 };
 
-// Gather map of level h: S_h(v)[s, rho''] accumulates c_h(u)[s, src] over
-// neighbours u, src = map[(c_v * k + c_u) * Bs[h] + rho''] (-1: no
-// contribution because c_u is not in the set).
+// Gather map of level h: S_h(v)[rho'', s] accumulates c_h(u)[src, s] over
+// neighbours u and every shape s, src = map[(c_v * k + c_u) * Bs[h] + rho'']
+// (-1: no contribution because c_u is not in the set).
 struct GatherLevel {
     std::vector<int16_t> map;
 };

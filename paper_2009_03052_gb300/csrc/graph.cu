@@ -132,6 +132,45 @@ __global__ void hub_chunks(const int64_t *row_ptr, int64_t n, const u128 *nch, c
     if (n_hubs == 0 && blockIdx.x == 0 && threadIdx.x == 0) hub_chunk0[0] = 0;
 }
 
+// Nodes of degree <= HUB_CHUNK by degree: a histogram of the degrees, then
+// each node takes the next slot of its degree's range (ranges in descending
+// order of degree; the order inside a range does not matter).
+__global__ void degree_hist_kernel(const int64_t *__restrict__ row_ptr, int64_t n, unsigned *hist)
+{
+    __shared__ unsigned sh[HUB_CHUNK + 1];
+    for (int i = threadIdx.x; i <= HUB_CHUNK; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        if (d <= HUB_CHUNK) atomicAdd(&sh[d], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= HUB_CHUNK; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void degree_order_kernel(const int64_t *__restrict__ row_ptr, int64_t n, unsigned *cursor,
+                                    uint4 *__restrict__ sched)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = row_ptr[v], d = row_ptr[v + 1] - e0;
+        if (d <= HUB_CHUNK)
+            sched[atomicAdd(&cursor[d], 1u)] =
+                make_uint4((uint32_t)v, (uint32_t)e0, (uint32_t)((uint64_t)e0 >> 32), (uint32_t)d);
+    }
+}
+
+// Hubs of more than HUB_SERIAL chunks (their chunk sums get a warp each).
+__global__ void big_hubs_kernel(const int64_t *__restrict__ hub_chunk0, int64_t n_hubs, unsigned *count,
+                                uint32_t *__restrict__ big)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_hubs;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (hub_chunk0[i + 1] - hub_chunk0[i] > HUB_SERIAL) big[atomicAdd(count, 1u)] = (uint32_t)i;
+}
+
 // Colouring: c_v = floor(k * x0 / 2^32), x0 the first Philox4x32-10 word at
 // counter (v, 0, 0, 0xC010) and key = seed.
 __global__ void color_kernel(int64_t n, int k, uint64_t seed, uint8_t *colors)
@@ -415,7 +454,35 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
                                            g->hub_node, g->hub_chunk0, g->node_chunk0, g->n_hubs, g->n_chunks));
         else
             MC_CUDA(cudaMemsetAsync(g->hub_chunk0, 0, sizeof(int64_t), s));
+        g->big_hub = g->arena.get<uint32_t>((size_t)std::max<int64_t>(g->n_hubs, 1));
+        unsigned nbig = 0;
+        if (g->n_hubs > 0) {
+            unsigned *dc = scratch.get<unsigned>(1);
+            MC_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned), s));
+            MC_LAUNCH("big_hubs", s, big_hubs_kernel<<<grid_for(g->n_hubs, 256), 256, 0, s>>>(
+                                         g->hub_chunk0, g->n_hubs, dc, g->big_hub));
+            MC_CUDA(cudaMemcpyAsync(&nbig, dc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        }
+        // the schedule of the neighbour sums: the other nodes by descending degree
+        g->n_small = n - g->n_hubs;
+        g->sched = g->arena.get<uint4>((size_t)std::max<int64_t>(g->n_small, 1));
+        unsigned hh[HUB_CHUNK + 1], cur[HUB_CHUNK + 1];  // live until the synchronisation below
+        if (g->n_small > 0) {
+            unsigned *dh = scratch.get<unsigned>(2 * (HUB_CHUNK + 1));
+            MC_CUDA(cudaMemsetAsync(dh, 0, (HUB_CHUNK + 1) * sizeof(unsigned), s));
+            MC_LAUNCH("degree_order", s, degree_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(g->row_ptr, n, dh));
+            MC_CUDA(cudaMemcpyAsync(hh, dh, sizeof(hh), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaStreamSynchronize(s));
+            g->n_big_hubs = nbig;
+            unsigned run = 0;
+            for (int d = HUB_CHUNK; d >= 0; --d) { cur[d] = run; run += hh[d]; }
+            MC_REQUIRE((int64_t)run == g->n_small, "degree histogram does not match the hub count");
+            MC_CUDA(cudaMemcpyAsync(dh + HUB_CHUNK + 1, cur, sizeof(cur), cudaMemcpyHostToDevice, s));
+            MC_LAUNCH("degree_order", s, degree_order_kernel<<<grid_for(n, 256), 256, 0, s>>>(
+                                             g->row_ptr, n, dh + HUB_CHUNK + 1, g->sched));
+        }
         MC_CUDA(cudaStreamSynchronize(s));
+        g->n_big_hubs = nbig;
     });
     if (st != MC_OK) { delete g; return st; }
     *out = g;

@@ -128,6 +128,9 @@ void refresh_tables(const mc_tables *t, cudaStream_t s, bool force = false);
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
 // sums are added afterwards (and kept as their prefix for the sampler).
 constexpr int HUB_CHUNK = 64;
+// Hubs of at most HUB_SERIAL chunks have their chunk sums added up by one
+// thread per S entry; larger ones (listed in big_hub) by a warp per entry.
+constexpr int HUB_SERIAL = 32;
 
 }  // namespace mc
 
@@ -143,6 +146,13 @@ struct mc_graph {
     uint32_t *hub_node = nullptr;
     int64_t *hub_chunk0 = nullptr;  // n_hubs + 1 entries
     int32_t *node_chunk0 = nullptr; // per node: its first chunk if it is a hub, else -1
+    // the nodes of degree <= HUB_CHUNK in descending order of degree (the
+    // schedule of the neighbour-sum kernel), n_small of them, one record each:
+    // (node, first edge low word, first edge high word, degree)
+    uint4 *sched = nullptr;
+    int64_t n_small = 0;
+    uint32_t *big_hub = nullptr;  // hubs (indices into hub_node) of more than HUB_SERIAL chunks
+    int64_t n_big_hubs = 0;
     mc::Arena arena;
     // uncoloured h-star index, built on first use: inclusive prefix over v of
     // C(d_v, h-1) and its total

@@ -303,6 +303,7 @@ struct SampleArgs {
     const void *Sp[MAXK + 1];   // per level: inclusive prefix of each hub's chunk sums
     const int32_t *node_chunk0; // first chunk of a hub, -1 for other nodes
     int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
+    int R_[MAXK + 1];           // rooted shapes per size: rows are set-major, entry (set, shape) at set * R_ + shape
     int k, h;
     const u128 *prefix;
     u128 R;                     // total of the node range sampled from
@@ -338,7 +339,7 @@ __device__ __forceinline__ V count_at(const SampleArgs &a, const SampleSmem &sm,
     if (hg == 1) return 1;
     const unsigned rel = drop_colour(C & ~(1u << cx), cx);
     const CT *row = (const CT *)a.c[hg] + (int64_t)x * a.Wc[hg];
-    return (V)row[a.loc[g] * a.Bc[hg] + sm.crank[rel]];
+    return (V)row[sm.crank[rel] * a.R_[hg] + a.loc[g]];
 }
 
 __device__ __forceinline__ uint64_t quotient(uint64_t a, uint64_t b) { return a / b; }
@@ -474,13 +475,14 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
         if (ok) {
             const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
             const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
-            const int Bc = a.Bc[h];
+            const int Bc = a.Bc[h], Rh = a.R_[h];
             V bf;
+            // e runs in (shape id, colour mask) order; the row is set-major
             const int found = lane_first_exceeding<V>(a.Wc[h], rem, [&](int e) -> V {
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
                 rb += al ? CB : 0;
-                return al ? (V)vrow[e] : (V)0;
+                return al ? (V)vrow[(e - sh * Bc) * Rh + sh] : (V)0;
             }, bf);
             if (found < 0) { ok = false; bad = true; }
             else {
@@ -527,13 +529,14 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                     int nsub = 1;
                     for (int i = 1; i <= hb; ++i) nsub = nsub * (nr - hb + i) / i;
                     const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
-                    sbase = a.loc[gb] * a.Bs[hb];
+                    sbase = a.loc[gb];
+                    const int Rb = a.R_[hb];
                     V before;
                     const int blk = lane_first_exceeding<V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
                         rb += 2 * CB;
                         return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) *
-                               (V)srow[sbase + sm.crank[drop_colour(c2, cx)]];
+                               (V)srow[sm.crank[drop_colour(c2, cx)] * Rb + sbase];
                     }, before);
                     if (blk < 0) { ok = false; bad = true; }
                     else {
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                         C1 = C & ~C2;
                         const V x1 = count_at<CT, V>(a, sm, ga, C1, x, cx);
                         q = (CT)quotient(Y - before, x1);  // < S(T'', C'', x): fits CT
-                        sidx = sbase + sm.crank[drop_colour(C2, cx)];
+                        sidx = sm.crank[drop_colour(C2, cx)] * a.R_[hb] + sbase;
                         if (chunk0 >= 0) nch = (e1 - e0 + HUB_CHUNK - 1) / HUB_CHUNK;
                     }
                 }
@@ -599,7 +602,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                 {
                     const int lb = a.loc[gb];
                     const CT *chb = (const CT *)a.c[hb];
-                    const int bcb = a.Bc[hb], wcb = a.Wc[hb];
+                    const int rcb = a.R_[hb], wcb = a.Wc[hb];
                     CT bn;
                     const int r = lane_first_exceeding<CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                         if (!((C2 >> cu) & 1u)) return (CT)0;
                         rb += 4 + CB;
                         const uint32_t u = a.col[lo_e + i];
-                        return chb[(int64_t)u * wcb + lb * bcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)]];
+                        return chb[(int64_t)u * wcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)] * rcb + lb];
                     }, bn);
                     if (r >= 0) sel = lo_e + r;
                 }
@@ -863,6 +866,7 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
         a.Bs[i] = t->geo.Bs[i];
         a.Wc[i] = t->geo.Wc[i];
         a.Ws[i] = t->geo.Ws[i];
+        a.R_[i] = cat.r[i];
     }
     a.k = t->k;
     a.h = h;

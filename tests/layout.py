@@ -50,27 +50,28 @@ def to_u128_pairs(a: np.ndarray) -> np.ndarray:
 
 
 def gpu_c_as_oracle(gpu: np.ndarray, colors: np.ndarray, k: int, h: int, r: int) -> np.ndarray:
-    """GPU level-h c table [n, r*Bc, words] -> oracle layout [n, r, C(k,h), 2]."""
+    """GPU level-h c table [n, Bc*r, words] (set-major: entry (set rho, shape s)
+    at rho * r + s) -> oracle layout [n, r, C(k,h), 2]."""
     n = gpu.shape[0]
     Bc = math.comb(k - 1, h - 1)
-    g = to_u128_pairs(gpu).reshape(n, r, Bc, 2)
+    g = to_u128_pairs(gpu).reshape(n, Bc, r, 2)               # set-major rows
     out = np.zeros((n, r, math.comb(k, h), 2), np.uint64)
     idx = c_index_map(k, h)[colors.astype(np.int64)]          # [n, Bc]
     rows = np.arange(n)[:, None]
     for s in range(r):
-        out[rows, s, idx] = g[:, s]
+        out[rows, s, idx] = g[:, :, s]
     return out
 
 
 def gpu_s_as_oracle(gpu: np.ndarray, colors: np.ndarray, k: int, h: int, r: int) -> np.ndarray:
     n = gpu.shape[0]
     Bs = math.comb(k - 1, h)
-    g = to_u128_pairs(gpu).reshape(n, r, Bs, 2)
+    g = to_u128_pairs(gpu).reshape(n, Bs, r, 2)               # set-major rows
     out = np.zeros((n, r, math.comb(k, h), 2), np.uint64)
     idx = s_index_map(k, h)[colors.astype(np.int64)]
     rows = np.arange(n)[:, None]
     for s in range(r):
-        out[rows, s, idx] = g[:, s]
+        out[rows, s, idx] = g[:, :, s]
     return out
 
 

@@ -61,7 +61,7 @@ def test_chung_lu_1m_k5_full_size(M, oracle):
         Bs = layout.s_index_map(k, h)
         for v in nodes:
             want = O.neighbor_sum(h, int(v))            # [r, C(k,h), 2]
-            got = gs[v].reshape(C.r(h), -1)            # [r, C(k-1,h)] u64
+            got = gs[v].reshape(-1, C.r(h)).T          # set-major row -> [r, C(k-1,h)] u64
             idx = Bs[int(colors[v])]
             assert np.array_equal(got, want[:, idx, 0]) and not want[:, idx, 1].any(), (h, v)
     gn, gr, gsh, gcl = T.sample(k, seed=7, first_index=0, count=3000)
