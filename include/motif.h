@@ -180,6 +180,31 @@ mc_status mc_build_tables_batch(int count, const mc_graph *const *graphs, const 
 mc_status mc_rebuild_tables(mc_tables *t, const uint8_t *colors, void *stream);
 mc_status mc_tables_status(const mc_tables *t, void *stream);
 
+/* Autotuning of the build's kernel schedules (no counterpart in the paper:
+ * the choice of GPU schedule).  The neighbour-sum and merge kernels of each
+ * level have a few schedules (lanes per node, rows in flight, registers per
+ * thread) that compute identical tables.  mc_build_tables times
+ * every candidate once for each new (kernel, k, count width, level, degree
+ * bucket) key and keeps the fastest; the degree bucket is floor(log2 n),
+ * floor(2 log2(nnz / n)) and floor(log2(max degree + 1)).  mc_rebuild_tables
+ * never tunes (it may be captured): it uses the choices made so far.
+ *   mode 0: never tune (choices loaded or made earlier, else the first
+ *           schedule); 1 (default): tune keys not seen yet; 2: tune every key
+ *           once more in this process.
+ *   cache_file (may be NULL: unchanged; "": stop appending): load its
+ *   choices now and append every new one to it; the MC_AUTOTUNE_CACHE
+ *   environment variable does the same at the first build.  One line per key: kind k bits h logn logdeg loghub choice.
+ * mc_autotune_choice: the schedule chosen so far for kernel kind (0 the
+ * neighbour sums, schedules 0..4; 1 the merge, schedules 0..2) at level h
+ * of tables with k colours and count_bits counts on graphs of n nodes, nnz
+ * adjacency entries and largest degree max_degree (mc_graph_info), or -1.
+ * mc_autotune_set: fix that choice (MC_E_INVALID for an unknown kind or
+ * schedule); builds use it and do not tune it again (in mode 1). */
+mc_status mc_autotune(int mode, const char *cache_file);
+int mc_autotune_choice(int kind, int k, int count_bits, int h, int64_t n, int64_t nnz, int64_t max_degree);
+mc_status mc_autotune_set(int kind, int k, int count_bits, int h, int64_t n, int64_t nnz, int64_t max_degree,
+                          int choice);
+
 /* Layout of the level-h table (which = 0: counts c, h = 1..k; which = 1:
  * neighbour sums S, h = 1..k-1).  Row v holds row_entries entries of
  * entry_bytes (8 or 16, little-endian, low word first).  Rows are

@@ -40,6 +40,7 @@ EXPORTED = [
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
     "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars", "mc_rebuild_tables",
     "mc_tables_status", "mc_color_biased", "mc_table_nonzeros", "mc_skip_round_info",
+    "mc_autotune", "mc_autotune_choice", "mc_autotune_set",
 ]
 
 
@@ -131,6 +132,9 @@ def load(path: str | None = None):
         lib.mc_skip_round_info.argtypes = [C.c_int, P, P, P, P, P, P]
         lib.mc_tables_status.argtypes = [P, P]
         lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
+        lib.mc_autotune.argtypes = [C.c_int, C.c_char_p]
+        lib.mc_autotune_choice.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, i64, i64, i64]
+        lib.mc_autotune_set.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, i64, i64, i64, C.c_int]
         _lib = lib
         return lib
 
@@ -510,6 +514,26 @@ def profile_read(with_bytes: bool = False) -> dict:
         v = (float(ms[i]), int(launches[i]))
         out[parts[i].decode()] = v + (int(nbytes[i]),) if with_bytes else v
     return out
+
+
+def autotune(mode: int = 1, cache_file: str | None = None):
+    """mc_autotune: 0 never tune, 1 tune new keys (default), 2 tune every key
+    once more; cache_file: load choices from it and append new ones ("" stops
+    appending)."""
+    _check(load().mc_autotune(mode, cache_file.encode() if cache_file is not None else None))
+
+
+def autotune_choice(kind: int, k: int, count_bits: int, h: int, n: int, nnz: int,
+                    max_degree: int) -> int:
+    """mc_autotune_choice: the schedule chosen for (kernel kind, k, width,
+    level h) on graphs of this size and degree bucket (-1: not tuned yet)."""
+    return int(load().mc_autotune_choice(kind, k, count_bits, h, n, nnz, max_degree))
+
+
+def autotune_set(kind: int, k: int, count_bits: int, h: int, n: int, nnz: int,
+                 max_degree: int, choice: int):
+    """mc_autotune_set: fix the schedule of one key."""
+    _check(load().mc_autotune_set(kind, k, count_bits, h, n, nnz, max_degree, choice))
 
 
 def launch_count() -> int:

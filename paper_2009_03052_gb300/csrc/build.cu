@@ -10,250 +10,25 @@
 // index structure is the same at every node and the gather reads only live
 // entries of the neighbour's row.
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
 
-#include "internal.h"
+#include "gather.cuh"
 
 namespace mc {
 
-enum : int { ERR_OVERFLOW = 1, ERR_INEXACT = 2, ERR_COLOUR = 4, ERR_SEARCH = 8 };
-
-// ---------------------------------------------------------------------------
-// Neighbour sums of level h >= 2 (the inner sum over u of Eq. 1):
-//   S_h(v)[rho'', s] = sum_{u ~ v} c_h(u)[map(c_v, c_u, rho''), s].
-// Rows are set-major, so the entries of one colour set (all r_h shapes) are
-// contiguous, and a neighbour u contributes whole sets: the S sets holding
-// c_u take u's sets that avoid c_v.  A row is handled in units of UB bytes
-// (16 when a set's bytes are a multiple of 16, else 8); a lane owns S units
-// j, j + G, ... of its node and, per neighbour, loads the one source unit
-// that feeds each (map in shared memory), U neighbours in flight.
-//   * nodes of degree <= HUB_CHUNK: G lanes per node, 32 / G nodes per warp,
-//     taken in the order `order` (descending degree, so the nodes of a warp
-//     have nearly equal degrees);
-//   * hub chunks (HUB_CHUNK consecutive neighbours of a hub): a warp per
-//     chunk, its 32 / G groups on different neighbours, summed by shuffles;
-//     the partial row goes to `partial`, entry-major per hub.
-// The first `chunk_blocks` blocks take the hub chunks, the rest the nodes.
-// ---------------------------------------------------------------------------
-struct GatherArgs {
-    const int64_t *row_ptr;
-    const uint32_t *col;
-    const uint8_t *colors;
-    const uint8_t *ecol;
-    const uint4 *sched;      // nodes of degree <= HUB_CHUNK, descending degree: (v, e0 lo, e0 hi, degree)
-    int64_t n_small;
-    const int32_t *node_chunk0;
-    const void *src;   // c_h, n x Wc
-    void *dst;         // S_h, n x Ws
-    void *partial;     // n_chunks x Ws
-    const uint32_t *chunk_node;
-    const int64_t *chunk_e0, *chunk_e1;
-    const int16_t *gmap;
-    int64_t n, n_chunks;
-    int k, Bs, Wc, Ws;
-    int ups;           // units per colour set
-    int wc_units, ws_units;
-    int chunk_blocks;
-    int *err;
-};
-
-// A unit of UB bytes of a row of CT counts, with exact (overflow-checked) adds.
-template <typename CT, int UB> struct Unit;
-template <> struct Unit<uint64_t, 8> {
-    uint64_t a;
-    __device__ __forceinline__ void zero() { a = 0; }
-    __device__ __forceinline__ void load(const void *p) { a = __ldg((const unsigned long long *)p); }
-    __device__ __forceinline__ bool add(const Unit &x) { return add_ovf(a, x.a); }
-    __device__ __forceinline__ void store(void *p) const { *(uint64_t *)p = a; }
-    __device__ __forceinline__ Unit xor_shfl(int d) const { Unit r; r.a = __shfl_xor_sync(0xffffffffu, a, d); return r; }
-    __device__ __forceinline__ uint64_t entry(int i) const { return a; }
-};
-template <> struct Unit<uint64_t, 16> {
-    uint64_t a, b;
-    __device__ __forceinline__ void zero() { a = b = 0; }
-    __device__ __forceinline__ void load(const void *p)
-    {
-        const ulonglong2 v = __ldg((const ulonglong2 *)p);
-        a = v.x;
-        b = v.y;
-    }
-    __device__ __forceinline__ bool add(const Unit &x)
-    {
-        const bool o1 = add_ovf(a, x.a);
-        const bool o2 = add_ovf(b, x.b);
-        return o1 | o2;
-    }
-    __device__ __forceinline__ void store(void *p) const { *(ulonglong2 *)p = make_ulonglong2(a, b); }
-    __device__ __forceinline__ Unit xor_shfl(int d) const
-    {
-        Unit r;
-        r.a = __shfl_xor_sync(0xffffffffu, a, d);
-        r.b = __shfl_xor_sync(0xffffffffu, b, d);
-        return r;
-    }
-    __device__ __forceinline__ uint64_t entry(int i) const { return i ? b : a; }
-};
-template <> struct Unit<u128, 16> {
-    u128 a;
-    __device__ __forceinline__ void zero() { a = 0; }
-    __device__ __forceinline__ void load(const void *p)
-    {
-        const ulonglong2 v = __ldg((const ulonglong2 *)p);
-        a = ((u128)v.y << 64) | v.x;
-    }
-    __device__ __forceinline__ bool add(const Unit &x) { return add_ovf(a, x.a); }
-    __device__ __forceinline__ void store(void *p) const
-    {
-        *(ulonglong2 *)p = make_ulonglong2((uint64_t)a, (uint64_t)(a >> 64));
-    }
-    __device__ __forceinline__ Unit xor_shfl(int d) const { Unit r; r.a = shfl_xor(a, d); return r; }
-    __device__ __forceinline__ u128 entry(int i) const { return a; }
-};
-
-template <typename CT, int UB, int G, int NU, int U>
-__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a)
+GatherKernel gather_kernel_ptr(size_t count_bytes, int UB, int G, int NU, int U, int MB)
 {
-    extern __shared__ int16_t s_map[];
-    const int mapn = a.k * a.k * a.Bs;
-    for (int i = threadIdx.x; i < mapn; i += blockDim.x) s_map[i] = a.gmap[i];
-    __syncthreads();
-
-    typedef Unit<CT, UB> UT;
-    constexpr int NG = 32 / G;
-    constexpr int EPU = UB / (int)sizeof(CT);  // entries per unit
-    const int lane = threadIdx.x & 31;
-    const int grp = lane / G, j = lane % G;
-    // the lane's units: set and unit within the set
-    int uset[NU], usub[NU];
-    bool own[NU];
-#pragma unroll
-    for (int i = 0; i < NU; ++i) {
-        const int un = j + i * G;
-        own[i] = un < a.ws_units;
-        uset[i] = own[i] ? un / a.ups : 0;
-        usub[i] = own[i] ? un - uset[i] * a.ups : 0;
-    }
-    const char *__restrict__ src = (const char *)a.src;
-    const int64_t rowb = (int64_t)a.wc_units * UB;
-    const int wpb = blockDim.x >> 5;
-    bool ovf = false;
-    UT acc[NU];
-
-    if ((int)blockIdx.x < a.chunk_blocks) {
-        // ---- hub chunks: a warp per chunk
-        for (int64_t t = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < a.n_chunks;
-             t += (int64_t)a.chunk_blocks * wpb) {
-            const int64_t v = a.chunk_node[t];
-            const int64_t e0 = a.chunk_e0[t], e1 = a.chunk_e1[t];
-            const int cv = a.colors[v];
-#pragma unroll
-            for (int i = 0; i < NU; ++i) acc[i].zero();
-            for (int64_t b = e0; b < e1; b += NG * U) {
-                UT x[U][NU];
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const int64_t e = b + q * NG + grp;
-                    const bool in = e < e1;
-                    const uint32_t u = in ? a.col[e] : 0u;
-                    const int cu = in ? (int)a.ecol[e] : cv;
-                    const int16_t *gm = s_map + (cv * a.k + cu) * a.Bs;
-#pragma unroll
-                    for (int i = 0; i < NU; ++i) {
-                        const int ss = (in && cu != cv && own[i]) ? gm[uset[i]] : -1;
-                        if (ss >= 0) x[q][i].load(src + (int64_t)u * rowb + (int64_t)(ss * a.ups + usub[i]) * UB);
-                        else x[q][i].zero();
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < U; ++q)
-#pragma unroll
-                    for (int i = 0; i < NU; ++i) ovf |= acc[i].add(x[q][i]);
-            }
-#pragma unroll
-            for (int d = G; d < 32; d <<= 1)
-#pragma unroll
-                for (int i = 0; i < NU; ++i) ovf |= acc[i].add(acc[i].xor_shfl(d));
-            if (grp == 0) {
-                // partial row of the chunk, entry-major per hub:
-                // [first chunk * Ws + entry * (chunks of the hub) + chunk]
-                const int64_t c0 = a.node_chunk0[v];
-                const int64_t nch = (a.row_ptr[v + 1] - a.row_ptr[v] + HUB_CHUNK - 1) / HUB_CHUNK;
-                CT *out = (CT *)a.partial + c0 * a.Ws + (t - c0);
-#pragma unroll
-                for (int i = 0; i < NU; ++i)
-                    if (own[i])
-#pragma unroll
-                        for (int w = 0; w < EPU; ++w)
-                            out[(int64_t)((j + i * G) * EPU + w) * nch] = acc[i].entry(w);
-            }
-        }
-        if (ovf) atomicOr(a.err, ERR_OVERFLOW);
-        return;
-    }
-
-    // ---- nodes of degree <= HUB_CHUNK: G lanes per node.  The ids and
-    // colours of the next U neighbours are loaded while the rows of the
-    // current U are in flight.
-    const int64_t nblk = (int64_t)gridDim.x - a.chunk_blocks;
-    const int64_t warp0 = ((int64_t)blockIdx.x - a.chunk_blocks) * wpb + (threadIdx.x >> 5);
-    for (int64_t base = warp0 * NG; base < a.n_small; base += nblk * wpb * NG) {
-        const int64_t idx = base + grp;
-        const bool valid = idx < a.n_small;
-        const uint4 rec = valid ? a.sched[idx] : make_uint4(0u, 0u, 0u, 0u);
-        const int64_t v = rec.x;
-        const int64_t e0 = (int64_t)(((uint64_t)rec.z << 32) | rec.y);
-        const int d = (int)rec.w;
-        const int cv = valid ? (int)a.colors[v] : 0;
-        const int dmax = __reduce_max_sync(0xffffffffu, (unsigned)d);
-#pragma unroll
-        for (int i = 0; i < NU; ++i) acc[i].zero();
-        uint32_t nu_[U];
-        int ncu[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const bool in = q < d;
-            nu_[q] = in ? a.col[e0 + q] : 0u;
-            ncu[q] = in ? (int)a.ecol[e0 + q] : cv;
-        }
-        for (int off = 0; off < dmax; off += U) {
-            uint32_t u[U];
-            int cu[U];
-#pragma unroll
-            for (int q = 0; q < U; ++q) { u[q] = nu_[q]; cu[q] = ncu[q]; }
-            UT x[U][NU];
-#pragma unroll
-            for (int q = 0; q < U; ++q) {
-                const int16_t *gm = s_map + (cv * a.k + cu[q]) * a.Bs;
-#pragma unroll
-                for (int i = 0; i < NU; ++i) {
-                    const int ss = (cu[q] != cv && own[i]) ? gm[uset[i]] : -1;
-                    if (ss >= 0) x[q][i].load(src + (int64_t)u[q] * rowb + (int64_t)(ss * a.ups + usub[i]) * UB);
-                    else x[q][i].zero();
-                }
-            }
-            if (off + U < dmax) {
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const bool in = off + U + q < d;
-                    nu_[q] = in ? a.col[e0 + off + U + q] : 0u;
-                    ncu[q] = in ? (int)a.ecol[e0 + off + U + q] : cv;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < U; ++q)
-#pragma unroll
-                for (int i = 0; i < NU; ++i) ovf |= acc[i].add(x[q][i]);
-        }
-        if (valid) {
-            char *out = (char *)a.dst + v * (int64_t)a.ws_units * UB;
-#pragma unroll
-            for (int i = 0; i < NU; ++i)
-                if (own[i]) acc[i].store(out + (int64_t)(j + i * G) * UB);
-        }
-    }
-    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (count_bytes == 16) return gather_kernel_ptr_u128_16(G, NU, U, MB);
+    return UB == 16 ? gather_kernel_ptr_u64_16(G, NU, U, MB) : gather_kernel_ptr_u64_8(G, NU, U, MB);
 }
 
+// The neighbour-sum kernel and its instantiations live in gather.cuh and
+// gather_*.cu.
 // Sum the chunk partials of each hub into its S row.  The chunk sums of a
 // (hub, S entry) pair are contiguous; they become their inclusive prefix
 // (the sampler binary-searches it) and the last prefix is the hub's
@@ -342,8 +117,8 @@ struct MergeArgs {
     int *err;
 };
 
-template <typename CT>
-__global__ void __launch_bounds__(256) merge_kernel(const __grid_constant__ MergeArgs a)
+template <typename CT, int MINB>
+__global__ void __launch_bounds__(256, MINB) merge_kernel(const __grid_constant__ MergeArgs a)
 {
     bool ovf = false, inexact = false;
     const int64_t total = a.n * a.W;
@@ -810,25 +585,37 @@ static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gat
 static const char *const kMergeName[MAXK + 1] = {"merge_h0", "merge_h1", "merge_h2", "merge_h3", "merge_h4",
                                                  "merge_h5", "merge_h6", "merge_h7", "merge_h8"};
 
-// Instantiations of the gather: G lanes per node (a power of two covering
-// the S row's units, at most 32), NU units per lane when a row has more than
-// 32 units, and U neighbours in flight (fewer when each lane owns many units).
-template <typename CT, int UB, int G, int NU>
-static void launch_gather_g(const GatherArgs &ga, int grid, size_t smem, const char *nm, cudaStream_t s)
-{
-    constexpr int U = NU >= 16 ? 1 : NU >= 8 ? 2 : NU >= 4 ? 4 : 8;
-    MC_LAUNCH(nm, s, gather_kernel<CT, UB, G, NU, U><<<grid, 256, smem, s>>>(ga));
-}
+static int rows_in_flight(int NU) { return NU >= 16 ? 1 : NU >= 8 ? 2 : NU >= 4 ? 4 : 8; }
+
+// Schedule candidates of the neighbour sums (the autotuner's choices), on
+// G0 lanes per node (the smallest power of two covering the row's units, at
+// most 32) and NU0 units per lane, with R0 = the standard rows in flight:
+//   0: R0 rows in flight, no register cap
+//   1: R0 / 2,  2: R0 / 4 (fewer registers, more warps per SM)
+//   3: R0 / 2 with at most 40 registers (6 blocks of 256 per SM)
+//   4: R0 / 4 with at most 32 registers (8 blocks of 256 per SM)
+constexpr int GATHER_CANDIDATES = 5;
 
 template <typename CT, int UB>
-static void launch_gather_ub(const GatherArgs &ga, int h, cudaStream_t s)
+static bool launch_gather_ub(const GatherArgs &ga, int h, int cand, cudaStream_t s)
 {
-    const char *nm = kGatherName[h];
     int G = 1;
     while (G < ga.ws_units && G < 32) G <<= 1;
     int NU = 1;
     while (NU * 32 < ga.ws_units) NU <<= 1;
     if (NU > 16) throw Error(MC_E_INTERNAL, "gather: S row too wide");
+    const int R0 = rows_in_flight(NU);
+    int U = R0, MB = 1;
+    switch (cand) {
+    case 0: break;
+    case 1: U = std::max(1, R0 / 2); break;
+    case 2: U = std::max(1, R0 / 4); break;
+    case 3: U = std::max(1, R0 / 2); MB = 6; break;
+    case 4: U = std::max(1, R0 / 4); MB = 8; break;
+    default: return false;
+    }
+    auto kern = gather_kernel_ptr(sizeof(CT), UB, G, NU, U, MB);
+    if (!kern) return false;
     const int NG = 32 / G;
     const int wpb = 256 / 32;
     GatherArgs g2 = ga;
@@ -837,35 +624,162 @@ static void launch_gather_ub(const GatherArgs &ga, int h, cudaStream_t s)
     const int64_t node_blocks = std::max<int64_t>(1, std::min<int64_t>((ga.n_small + NG * wpb - 1) / (NG * wpb), cap));
     const int grid = (int)(g2.chunk_blocks + node_blocks);
     const size_t smem = (size_t)ga.k * ga.k * ga.Bs * sizeof(int16_t);
-    switch (G) {
-    case 1: launch_gather_g<CT, UB, 1, 1>(g2, grid, smem, nm, s); break;
-    case 2: launch_gather_g<CT, UB, 2, 1>(g2, grid, smem, nm, s); break;
-    case 4: launch_gather_g<CT, UB, 4, 1>(g2, grid, smem, nm, s); break;
-    case 8: launch_gather_g<CT, UB, 8, 1>(g2, grid, smem, nm, s); break;
-    case 16: launch_gather_g<CT, UB, 16, 1>(g2, grid, smem, nm, s); break;
-    default:
-        switch (NU) {
-        case 1: launch_gather_g<CT, UB, 32, 1>(g2, grid, smem, nm, s); break;
-        case 2: launch_gather_g<CT, UB, 32, 2>(g2, grid, smem, nm, s); break;
-        case 4: launch_gather_g<CT, UB, 32, 4>(g2, grid, smem, nm, s); break;
-        case 8: launch_gather_g<CT, UB, 32, 8>(g2, grid, smem, nm, s); break;
-        default: launch_gather_g<CT, UB, 32, 16>(g2, grid, smem, nm, s); break;
-        }
-    }
+    MC_LAUNCH(kGatherName[h], s, kern<<<grid, 256, smem, s>>>(g2));
+    return true;
 }
 
-template <typename CT> static void launch_gather(GatherArgs &ga, const mc_graph *g, int r, int h, cudaStream_t s)
+template <typename CT> static bool launch_gather(GatherArgs &ga, int r, int h, int cand, cudaStream_t s)
 {
     const int B = (int)sizeof(CT);
     const int UB = (r * B) % 16 == 0 ? 16 : 8;  // a unit never straddles two colour sets
     ga.ups = r * B / UB;
     ga.wc_units = ga.Wc * B / UB;
     ga.ws_units = ga.Ws * B / UB;
-    if (UB == 16) launch_gather_ub<CT, 16>(ga, h, s);
-    else launch_gather_ub<uint64_t, 8>(ga, h, s);
+    if (UB == 16) return launch_gather_ub<CT, 16>(ga, h, cand, s);
+    return launch_gather_ub<uint64_t, 8>(ga, h, cand, s);
 }
 
-template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStream_t s)
+// Merge candidates: occupancy targets of 1 (no register cap), 6 and 8
+// blocks of 256 threads per SM.
+constexpr int MERGE_CANDIDATES = 3;
+
+template <typename CT> static bool launch_merge(const MergeArgs &ma, int h, int cand, cudaStream_t s)
+{
+    const int grid = grid_for(ma.n * ma.W, 256);
+    switch (cand) {
+    case 0: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 1><<<grid, 256, 0, s>>>(ma)); return true;
+    case 1: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 6><<<grid, 256, 0, s>>>(ma)); return true;
+    case 2: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 8><<<grid, 256, 0, s>>>(ma)); return true;
+    default: return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the schedule of each (kernel, k, count width, level, graph
+// shape) is chosen by timing every candidate once on the first build that
+// meets it (the candidates compute identical tables, so which one runs does
+// not change any result).  The graph's shape is reduced to a degree bucket:
+// log2 n, log2 of the average degree in half steps, log2 of the largest
+// degree.  Choices can be loaded from and appended to a cache file
+// (mc_autotune, or the MC_AUTOTUNE_CACHE environment variable).
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int kind, k, bits, h, logn, logdeg, loghub;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(kind, k, bits, h, logn, logdeg, loghub) <
+               std::tie(o.kind, o.k, o.bits, o.h, o.logn, o.logdeg, o.loghub);
+    }
+};
+struct TuneState {
+    std::mutex mu;
+    std::map<TuneKey, int> choice;
+    std::set<TuneKey> retuned;  // mode 2: keys tuned again in this process
+    int mode = 1;               // 0 never tune, 1 tune unknown keys, 2 tune every key once more
+    std::string file;
+    bool env_read = false;
+};
+TuneState &tune_state()
+{
+    static TuneState st;
+    return st;
+}
+
+void tune_load_file_locked(TuneState &st, const std::string &path)
+{
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    TuneKey k{};
+    int v = 0;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.kind, &k.k, &k.bits, &k.h, &k.logn, &k.logdeg, &k.loghub,
+                       &v) == 8)
+        st.choice[k] = v;
+    std::fclose(f);
+}
+
+void tune_env_locked(TuneState &st)
+{
+    if (st.env_read) return;
+    st.env_read = true;
+    const char *p = std::getenv("MC_AUTOTUNE_CACHE");
+    if (p && *p) {
+        st.file = p;
+        tune_load_file_locked(st, st.file);
+    }
+}
+
+int ilog2(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
+}  // namespace
+
+static TuneKey tune_key(int kind, int k, int count_bits, int h, int64_t n, int64_t nnz, int64_t max_degree)
+{
+    const double nn = (double)std::max<int64_t>(n, 1);
+    return TuneKey{kind, k, count_bits, h, ilog2((double)n), ilog2((double)nnz * (double)nnz / (nn * nn)),
+                   ilog2((double)max_degree + 1)};
+}
+
+// Run `launch(candidate)` for the tuned candidate of `key`; when tuning is
+// allowed and the key is new (or mode 2), time every candidate first.
+template <typename F>
+static void run_tuned(TuneKey key, int ncand, bool allow, cudaStream_t s, F &&launch)
+{
+    TuneState &st = tune_state();
+    int v = -1;
+    bool tune = false;
+    {
+        std::lock_guard<std::mutex> lock(st.mu);
+        tune_env_locked(st);
+        auto it = st.choice.find(key);
+        if (it != st.choice.end()) v = it->second;
+        tune = allow && st.mode > 0 && (v < 0 || (st.mode == 2 && !st.retuned.count(key)));
+    }
+    if (tune) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        MC_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) tune = false;
+    }
+    if (tune) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        MC_CUDA(cudaEventCreate(&e0));
+        MC_CUDA(cudaEventCreate(&e1));
+        // three rounds over the candidates, each candidate's best time
+        // counts: every candidate meets the caches as the others left them
+        float best[8];
+        bool ok[8];
+        for (int c = 0; c < ncand && c < 8; ++c) { best[c] = 0.f; ok[c] = true; }
+        for (int rep = 0; rep < 3; ++rep)
+            for (int c = 0; c < ncand && c < 8; ++c) {
+                if (!ok[c]) continue;
+                MC_CUDA(cudaEventRecord(e0, s));
+                if (!launch(c)) { ok[c] = false; continue; }
+                MC_CUDA(cudaEventRecord(e1, s));
+                MC_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                MC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep == 0 || ms < best[c]) best[c] = ms;
+            }
+        int bv = -1;
+        for (int c = 0; c < ncand && c < 8; ++c)
+            if (ok[c] && (bv < 0 || best[c] < best[bv])) bv = c;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        v = bv < 0 ? 0 : bv;
+        std::lock_guard<std::mutex> lock(st.mu);
+        st.choice[key] = v;
+        st.retuned.insert(key);
+        if (!st.file.empty()) {
+            if (FILE *f = std::fopen(st.file.c_str(), "a")) {
+                std::fprintf(f, "%d %d %d %d %d %d %d %d\n", key.kind, key.k, key.bits, key.h, key.logn, key.logdeg,
+                             key.loghub, v);
+                std::fclose(f);
+            }
+        }
+    }
+    if (v < 0 || !launch(v)) launch(0);
+}
+
+template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStream_t s, bool allow_tune)
 {
     const mc_graph *g = t->g;
     const Geometry &G = t->geo;
@@ -908,7 +822,8 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
         ma.Bc = G.Bc[h];
         ma.R = shape_catalog().r[h];
         ma.zero_root_colors = (t->zero_root && h == k) ? t->colors : nullptr;
-        MC_LAUNCH(kMergeName[h], s, merge_kernel<CT><<<grid_for(n * G.Wc[h], 256), 256, 0, s>>>(ma));
+        const TuneKey mkey = tune_key(1, k, (int)sizeof(CT) * 8, h, n, g->nnz, g->max_degree);
+        run_tuned(mkey, MERGE_CANDIDATES, allow_tune, s, [&](int c) { return launch_merge<CT>(ma, h, c, s); });
         if (h <= k - 1) {
             GatherArgs ga{};
             ga.row_ptr = g->row_ptr;
@@ -932,7 +847,9 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
             ga.err = err;
             ga.sched = g->sched;
             ga.n_small = g->n_small;
-            launch_gather<CT>(ga, g, shape_catalog().r[h], h, s);
+            const TuneKey gkey = tune_key(0, k, (int)sizeof(CT) * 8, h, n, g->nnz, g->max_degree);
+            const int rh = shape_catalog().r[h];
+            run_tuned(gkey, GATHER_CANDIDATES, allow_tune, s, [&](int c) { return launch_gather<CT>(ga, rh, h, c, s); });
             if (g->n_hubs) {
                 MC_LAUNCH("hub_reduce", s, hub_reduce_small_kernel<CT><<<grid_for(g->n_hubs * G.Ws[h], 256), 256, 0, s>>>(
                     (CT *)t->Sp[h], (CT *)t->S[h], g->hub_node, g->hub_chunk0, g->n_hubs, G.Ws[h], err));
@@ -952,7 +869,7 @@ using namespace mc;
 // Every launch of a build for the colours in `colors`, on stream s, into the
 // buffers of t: no allocation, no host read, no synchronisation (so a
 // rebuild can be captured into a CUDA graph).
-static void enqueue_build(mc_tables *t, const uint8_t *colors, cudaStream_t s)
+static void enqueue_build(mc_tables *t, const uint8_t *colors, cudaStream_t s, bool allow_tune)
 {
     const mc_graph *g = t->g;
     const int64_t n = g->n;
@@ -968,8 +885,8 @@ static void enqueue_build(mc_tables *t, const uint8_t *colors, cudaStream_t s)
     if (g->nnz)
         MC_LAUNCH("edge_colours", s, edge_colours_kernel<<<grid_for(g->nnz, 256), 256, 0, s>>>(
                                          g->col, t->colors, g->nnz, t->ecol));
-    if (t->bits == 64) build_levels<uint64_t>(t, err, s);
-    else build_levels<u128>(t, err, s);
+    if (t->bits == 64) build_levels<uint64_t>(t, err, s, allow_tune);
+    else build_levels<u128>(t, err, s, allow_tune);
     // root index of the top level (the level sampled by default); the other
     // levels get theirs on first use
     if (n) {
@@ -1066,7 +983,7 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         t->nbucket = bucket_count(n);
         t->prefix[k] = t->arena.get<u128>((size_t)n);
         t->bucket[k] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
-        enqueue_build(t, colors, s);
+        enqueue_build(t, colors, s, true);
         finish_build(t, s);
     });
     if (st != MC_OK) { delete t; return st; }
@@ -1080,7 +997,7 @@ extern "C" mc_status mc_rebuild_tables(mc_tables *t, const uint8_t *colors, void
         MC_REQUIRE(t, "tables is NULL");
         MC_REQUIRE(colors || t->g->n == 0, "colors is NULL");
         std::lock_guard<std::mutex> lock(t->idx_mu);
-        enqueue_build(t, colors, (cudaStream_t)stream);
+        enqueue_build(t, colors, (cudaStream_t)stream, false);
         t->stale = true;
         t->broken.clear();
         for (int h = 2; h < t->k; ++h) t->level_stale[h] = t->prefix[h] != nullptr;
@@ -1402,5 +1319,45 @@ extern "C" mc_status mc_read_table(const mc_tables *t, int h, int which, void *d
             MC_CUDA(cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         }
         MC_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+extern "C" mc_status mc_autotune(int mode, const char *cache_file)
+{
+    return guarded([&] {
+        MC_REQUIRE(mode >= 0 && mode <= 2, "mode must be 0, 1 or 2");
+        TuneState &st = tune_state();
+        std::lock_guard<std::mutex> lock(st.mu);
+        tune_env_locked(st);
+        st.mode = mode;
+        if (mode == 2) st.retuned.clear();
+        if (cache_file) {  // "" stops appending
+            st.file = cache_file;
+            if (!st.file.empty()) tune_load_file_locked(st, st.file);
+        }
+    });
+}
+
+extern "C" int mc_autotune_choice(int kind, int k, int count_bits, int h, int64_t n, int64_t nnz, int64_t max_degree)
+{
+    const TuneKey key = tune_key(kind, k, count_bits, h, n, nnz, max_degree);
+    TuneState &st = tune_state();
+    std::lock_guard<std::mutex> lock(st.mu);
+    tune_env_locked(st);
+    auto it = st.choice.find(key);
+    return it == st.choice.end() ? -1 : it->second;
+}
+
+extern "C" mc_status mc_autotune_set(int kind, int k, int count_bits, int h, int64_t n, int64_t nnz,
+                                     int64_t max_degree, int choice)
+{
+    return guarded([&] {
+        MC_REQUIRE(kind == 0 || kind == 1, "kind must be 0 (neighbour sums) or 1 (merge)");
+        MC_REQUIRE(choice >= 0 && choice < (kind == 0 ? GATHER_CANDIDATES : MERGE_CANDIDATES), "no such schedule");
+        const TuneKey key = tune_key(kind, k, count_bits, h, n, nnz, max_degree);
+        TuneState &st = tune_state();
+        std::lock_guard<std::mutex> lock(st.mu);
+        tune_env_locked(st);
+        st.choice[key] = choice;
     });
 }

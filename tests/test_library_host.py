@@ -90,3 +90,25 @@ def test_header_is_plain_c_and_cpp(tmp_path):
         r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_autotune_choices_cache_file(motif, tmp_path):
+    # the schedule table (host code): choices loaded from a cache file, pinned
+    # by mc_autotune_set, appended by the library; unknown schedules refused
+    path = tmp_path / "tune.txt"
+    n, nnz, maxd = 1_000_000, 19_970_150, 9529
+    # key fields: kind k bits h floor(log2 n) floor(2 log2(nnz/n)) floor(log2(maxd+1)) choice
+    path.write_text("0 5 64 3 19 8 13 2\n1 5 64 4 19 8 13 1\n")
+    motif.autotune(1, str(path))
+    assert motif.autotune_choice(0, 5, 64, 3, n, nnz, maxd) == 2
+    assert motif.autotune_choice(1, 5, 64, 4, n, nnz, maxd) == 1
+    assert motif.autotune_choice(0, 5, 64, 2, n, nnz, maxd) == -1
+    # the same degree bucket: another graph of the same shape
+    assert motif.autotune_choice(0, 5, 64, 3, n + 1000, nnz + 5000, maxd + 10) == 2
+    motif.autotune_set(0, 6, 128, 4, n, nnz, maxd, 2)
+    assert motif.autotune_choice(0, 6, 128, 4, n, nnz, maxd) == 2
+    with pytest.raises(motif.MotifError):
+        motif.autotune_set(1, 6, 128, 4, n, nnz, maxd, 3)   # the merge has schedules 0..2
+    with pytest.raises(motif.MotifError):
+        motif.autotune(3)
+    motif.autotune(1, "")
