@@ -179,10 +179,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
-def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int, step_samples: int = SAMPLES):
-    """Time the oracle on the workload: its table build on the full graph
-    plus n_samples uniform samples with classification; the sampling time
-    is scaled to the step's step_samples."""
+def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int):
+    """Time the oracle on one bounded step of the workload, as run (nothing
+    extrapolated): its table build on the full graph, then n_samples uniform
+    samples with classification and estimates.  Returns the step's DP-table
+    entries per second of step time, and the build and sampling rates."""
     import oracle
     oracle.build()
     oracle.class_codes(k)  # class list precomputed outside the timing
@@ -194,10 +195,13 @@ def oracle_step_rate(graph, k: int, n_samples: int, seed: int, threads: int, ste
     T.estimate_uniform(k, seed=seed, n_samples=n_samples)
     t2 = time.perf_counter()
     build_s, samp_s = t1 - t0, t2 - t1
-    step_s = build_s + samp_s * (step_samples / n_samples)
     entries = graph.n * live_entries_per_node(k)
-    return {"value": entries / step_s, "build_s": build_s, "sample_s": samp_s,
-            "step_s_equiv": step_s}
+    return {"value": entries / (build_s + samp_s), "build_s": build_s, "sample_s": samp_s,
+            "step_s": build_s + samp_s, "build_entries_per_s": entries / build_s,
+            "samples_per_s": n_samples / samp_s}
+
+
+ORACLE_STEP_SAMPLES = 2000  # samples in one bounded oracle step (about 0.5 s of its sampling)
 
 
 def run_reference(args, rank: int, world: int):
@@ -205,27 +209,29 @@ def run_reference(args, rank: int, world: int):
         return
     graph, wname = workload_graph(args.small)
     threads = os.cpu_count() or 1
-    n_samp = 1000 if not args.small else 10_000
+    k = K if not args.small else 4
+    n_samp = ORACLE_STEP_SAMPLES if not args.small else 10_000
     # warm-up: the oracle on a small graph of the same family
     warm = synth.chung_lu_scaled(5000, seed=1)
     for i in range(args.warmup):
         oracle_step_rate(warm, K, 100, 100 + i, threads)
-    step_samples = SAMPLES if not args.small else 10_000
-    res = [oracle_step_rate(graph, K if not args.small else 4, n_samp, 10 + i, threads, step_samples)
-           for i in range(args.steps)]
-    val = statistics.median(r["value"] for r in res)
-    step_ms = statistics.median(r["step_s_equiv"] for r in res) * 1e3
-    sample = (f"oracle build of the full {wname} graph plus {n_samp} samples per step; "
-              f"sampling time scaled to {step_samples} samples")
+    res = [oracle_step_rate(graph, k, n_samp, 10 + i, threads) for i in range(args.steps)]
+    step_s = sum(r["step_s"] for r in res)
+    entries = graph.n * live_entries_per_node(k)
+    val = entries * args.steps / step_s
+    sample = (f"one step = the oracle's build of the full {wname} graph plus {n_samp} uniform samples "
+              f"with classification and estimates, as run (the GPU step draws "
+              f"{SAMPLES if not args.small else 10_000})")
     line = {
         "impl": "reference", "metric": "DP table entries/s", "value": val,
         "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u128", "data": "synthetic",
-        "config": workload_config(graph, wname, K if not args.small else 4, SAMPLES if not args.small else 10_000,
-                                  args, world),
+        "ms_per_step": step_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(graph, wname, k, SAMPLES if not args.small else 10_000, args, world),
         "cpu_baseline": {"value": val, "unit": "entries/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample,
+                         "build_entries_per_s": statistics.median(r["build_entries_per_s"] for r in res),
+                         "samples_per_s": statistics.median(r["samples_per_s"] for r in res)},
         "e2e": {"value": val, "unit": "entries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -336,7 +342,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         if by is None:
             return None
         achieved = by / (ms / cnt / 1e3) / 1e9
-        traffic = TRAFFIC.get((wname, nm))
+        traffic = traffic_of(wname, nm)
         out = {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                "traffic": traffic, "algorithmic_bytes": int(by),
@@ -384,12 +390,27 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        n_samp = 1000 if not args.small else 10_000
-        r = oracle_step_rate(graph, k, n_samp, 5, threads, samples)
+        n_samp = ORACLE_STEP_SAMPLES if not args.small else 10_000
+        r = oracle_step_rate(graph, k, n_samp, 5, threads)
         cpu = {"value": r["value"], "unit": "entries/s", "cores": threads, "kind": "oracle",
-               "sample": (f"oracle build of the full {wname} graph ({r['build_s']:.1f} s) plus "
-                          f"{n_samp} samples ({r['sample_s']:.2f} s), sampling scaled to "
-                          f"{samples} samples per step")}
+               "sample": (f"one bounded step as run: the oracle's build of the full {wname} graph "
+                          f"({r['build_s']:.2f} s) plus {n_samp} uniform samples with classification "
+                          f"and estimates ({r['sample_s']:.2f} s)"),
+               "build_entries_per_s": r["build_entries_per_s"], "samples_per_s": r["samples_per_s"]}
+
+    # the schedules the autotuner chose for this workload's levels
+    gn, gnnz, gmaxd = G.info()
+    schedules = {}
+    for h in range(2, k + 1):
+        schedules[f"merge_h{h}"] = M.autotune_choice(1, k, BITS, h, gn, gnnz, gmaxd)
+        if h < k:
+            schedules[f"gather_h{h}"] = M.autotune_choice(0, k, BITS, h, gn, gnnz, gmaxd)
+
+    extra = {}
+    if rank == 0 and not args.no_extra and not args.small:
+        del G
+        torch.cuda.empty_cache()
+        extra = extra_workloads(M, torch)
 
     if world > 1:
         dist.destroy_process_group()
@@ -411,9 +432,69 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.median(e2e_ms),
                 "path": "mc_load_graph (pinned host CSR, trusted) + mc_color + mc_build_tables + "
                         "mc_estimate_counts (host estimates)"},
-        "cpu_baseline": cpu, "clocks": clk,
+        "cpu_baseline": cpu, "clocks": clk, "schedules": schedules,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def extra_workloads(M, torch) -> dict:
+    """k = 7 and k = 8 beside the k = 5 line (u128 counts): build entries/s,
+    uniform and adaptive (AGS) colourful graphlet samples/s.
+      k7_rmat22: R-MAT scale 22, edge factor 16 (a, b, c = .57, .19, .19);
+                 10M uniform samples, AGS with cbar = 1000 and 10M samples.
+      k8_cl2m:   Chung-Lu n = 2M, m ~ 20M, exponent 2.5; 1M uniform
+                 8-samples, AGS with cbar = 1000 and 1M samples.
+    Builds: one warm-up (it autotunes), then the median of two; L2 flushed
+    before each timed call."""
+    out = {}
+    s = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        flush.fill_(7)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        r = fn()
+        b.record(s)
+        b.synchronize()
+        return a.elapsed_time(b), r
+
+    for name, make, k, uni, ags in (
+            ("k7_rmat22", lambda: synth.rmat(22, 16, seed=0), 7, 10_000_000, 10_000_000),
+            ("k8_cl2m", lambda: synth.chung_lu(2_000_000, 20_000_000, 2.5, max_degree=10_000.0, seed=0),
+             8, 1_000_000, 1_000_000)):
+        g = make()
+        G = M.Graph.from_csr(g, trusted=True)
+        col = M.color(G, k, 11)
+        M.sigma(k)
+        T = M.Tables(G, col, k, 128)  # warm-up build (autotunes)
+        T.free()
+        bms = []
+        for _ in range(2):
+            ms, T = timed(lambda: M.Tables(G, col, k, 128))
+            bms.append(ms)
+            if _ == 0:
+                T.free()
+        T.total(k)
+        for j in range(M.num_unrooted(k)):
+            T.total(k, j)
+        T.estimate(k, seed=1, samples=100_000)  # warm-up of the samplers
+        T.estimate(k, seed=1, samples=100_000, mode=M.MC_EST_AGS, cbar=1000)
+        ums, _ = timed(lambda: T.estimate(k, seed=2, samples=uni))
+        ams, (_, _, st) = timed(lambda: T.estimate(k, seed=3, samples=ags, mode=M.MC_EST_AGS, cbar=1000))
+        T.free()
+        entries = g.n * live_entries_per_node(k)
+        bm = statistics.median(bms)
+        out[name] = {"n": g.n, "m": g.m, "k": k, "count_bits": 128, "build_ms": round(bm, 3),
+                     "build_entries_per_s": entries / (bm / 1e3),
+                     "uniform_samples": uni, "uniform_samples_per_s": uni / (ums / 1e3),
+                     "ags_samples": st["samples"], "ags_samples_per_s": st["samples"] / (ams / 1e3),
+                     "ags_switches": st["switches"], "ags_over_uniform_speed": (st["samples"] / ams) / (uni / ums)}
+        del G
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -662,13 +743,27 @@ def run_serve(args):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from
-# one ncu --set full capture of the named kernel on the named workload
-# (profiles/sample_kernel_chung_lu_1m_k5.md, profiles/gather_kernel_h3_chung_lu_1m_k5.md);
-# remove an entry when its kernel changes.
-TRAFFIC: dict = {
-    ("chung_lu_1m_k5", "sample"): 2_599_895_352,     # 1M samples, 2.153 GB read + 0.447 GB written
-    ("chung_lu_1m_k5", "gather_h3"): 804_434_176,    # 0.737 GB read + 0.067 GB written
-}
+# one ncu capture of the named kernel on the named workload (the summaries in
+# profiles/), with a hash of the kernel's source file when it was captured:
+# the figure is reported only while that source is unchanged.
+TRAFFIC: dict = {}
+KERNEL_SOURCE = {"sample": "sample.cu", "gather": "gather.cuh", "merge": "build.cu"}
+
+
+def source_hash(kernel: str) -> str:
+    import hashlib
+    base = kernel.split("_h")[0]
+    path = os.path.join(ROOT, "paper_2009_03052_gb300", "csrc", KERNEL_SOURCE.get(base, ""))
+    if not os.path.isfile(path):
+        return ""
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_of(workload: str, kernel: str):
+    entry = TRAFFIC.get((workload, kernel))
+    if not entry or entry[1] != source_hash(kernel):
+        return None
+    return entry[0]
 
 
 def main():
@@ -687,6 +782,8 @@ def main():
     ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the k = 7 (R-MAT 22) and k = 8 (Chung-Lu 2M) keys")
     ap.add_argument("--zero-root", action="store_true",
                     help="store level k at colour-0 nodes only (Section 3.4.1)")
     ap.add_argument("--skip-round", action="store_true",
