@@ -485,6 +485,19 @@ def extra_workloads(M, torch) -> dict:
         ums, _ = timed(lambda: T.estimate(k, seed=2, samples=uni))
         ams, (_, _, st) = timed(lambda: T.estimate(k, seed=3, samples=ags, mode=M.MC_EST_AGS, cbar=1000))
         T.free()
+        packed = {}
+        if k == 7:
+            # the same tables zero-suppressed (Section 3.2.1), with the
+            # table's width or each row's own width (Section 3.3.3)
+            for pname, vl in (("succinct", False), ("varlen", True)):
+                pms, P = timed(lambda: M.Tables(G, col, k, 128, succinct=True, varlen=vl))
+                dense_b, stored_b = P.table_bytes()
+                P.estimate(k, seed=1, samples=100_000)
+                pums, _ = timed(lambda: P.estimate(k, seed=2, samples=1_000_000))
+                packed[pname] = {"build_ms": round(pms, 3), "dense_bytes": dense_b, "stored_bytes": stored_b,
+                                 "stored_over_dense": round(stored_b / dense_b, 4),
+                                 "uniform_samples_per_s": 1_000_000 / (pums / 1e3)}
+                P.free()
         entries = g.n * live_entries_per_node(k)
         bm = statistics.median(bms)
         out[name] = {"n": g.n, "m": g.m, "k": k, "count_bits": 128, "build_ms": round(bm, 3),
@@ -492,6 +505,7 @@ def extra_workloads(M, torch) -> dict:
                      "uniform_samples": uni, "uniform_samples_per_s": uni / (ums / 1e3),
                      "ags_samples": st["samples"], "ags_samples_per_s": st["samples"] / (ams / 1e3),
                      "ags_switches": st["switches"], "ags_over_uniform_speed": (st["samples"] / ams) / (uni / ums)}
+        out[name].update(packed)
         del G
         torch.cuda.empty_cache()
     return out

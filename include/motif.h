@@ -105,7 +105,8 @@ mc_status mc_color_biased(const mc_graph *g, int k, uint64_t seed, uint32_t lamb
  * S(T'', C'', v) = sum_{u ~ v} c(T''_{C''}, u) and the disjoint-colour merge
  * c(T_C, v) = (1/beta_T) sum_{C' + C'' = C} c(T'_{C'}, v) S(T'', C'', v).
  * colors: device uint8[n] with values < k (read during the call only).
- * count_bits: 64 or 128.  flags: 0, MC_BUILD_ZERO_ROOT or MC_BUILD_SKIP_ROUND.  The tables stay on the device
+ * count_bits: 64 or 128.  flags: 0 or MC_BUILD_ZERO_ROOT or MC_BUILD_SKIP_ROUND, each
+ * optionally with MC_BUILD_SUCCINCT or MC_BUILD_VARLEN.  The tables stay on the device
  * until mc_free_tables; they are immutable, so concurrent readers are safe.
  * The graph must outlive the tables. */
 /* Zero-rooting (Section 3.4.1): keep the level-k counts only at nodes of
@@ -127,10 +128,28 @@ mc_status mc_color_biased(const mc_graph *g, int k, uint64_t seed, uint32_t lamb
  * with mc_sample_stars and estimated from those samples (star_samples in
  * mc_estimate_params). */
 #define MC_BUILD_SKIP_ROUND 0x2u
+/* Succinct tables (Section 3.2.1): once built, every level of c and S is
+ * kept as its non-zero entries only -- per node row, the entries' keys (their
+ * index in the dense row of mc_table_layout) in ascending order and their
+ * counts at the table's width -- and the dense levels are freed.  Sampling
+ * finds an entry by binary search of its row's keys; results are the same as
+ * from dense tables.  mc_read_table still returns dense rows;
+ * mc_table_nonzeros is the packed size; mc_table_bytes reports the
+ * footprint.  Such tables cannot be rebuilt in place (MC_E_UNSUPPORTED). */
+#define MC_BUILD_SUCCINCT 0x4u
+/* Variable-length counts (Section 3.3.3), implies MC_BUILD_SUCCINCT: each
+ * packed row stores its counts in the fewest of 1, 2, 4, 8 or 16 bytes that
+ * hold the row's largest count (the paper gives each count its own byte
+ * length; a per-row width keeps every load aligned). */
+#define MC_BUILD_VARLEN 0x8u
 
 mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, int k, int count_bits,
                           uint32_t flags, const mc_allocator *alloc, void *stream,
                           mc_tables **out);
+/* Device bytes of the c and S levels: as dense rows (n x row entries x count
+ * bytes per level) and as stored (the same for dense tables; keys, counts and
+ * row offsets for succinct ones).  Host int64 outputs, either may be NULL. */
+mc_status mc_table_bytes(const mc_tables *t, int64_t *dense_bytes, int64_t *stored_bytes);
 void mc_free_tables(mc_tables *t);
 
 /* Totals (the occ() queries of Section 3): rooted = sum over v and over the

@@ -26,6 +26,8 @@ MC_GRAPH_DEVICE_PTRS = 1
 MC_GRAPH_TRUSTED = 2
 MC_BUILD_ZERO_ROOT = 1
 MC_BUILD_SKIP_ROUND = 2
+MC_BUILD_SUCCINCT = 4
+MC_BUILD_VARLEN = 8
 MC_REQ_SAMPLE = 0
 MC_REQ_ESTIMATE = 1
 MC_EST_UNIFORM = 0
@@ -40,7 +42,7 @@ EXPORTED = [
     "mc_sample_range", "mc_build_tables_batch", "mc_server_create", "mc_server_submit",
     "mc_server_wait", "mc_server_free", "mc_star_total", "mc_sample_stars", "mc_rebuild_tables",
     "mc_tables_status", "mc_color_biased", "mc_table_nonzeros", "mc_skip_round_info",
-    "mc_autotune", "mc_autotune_choice", "mc_autotune_set",
+    "mc_autotune", "mc_autotune_choice", "mc_autotune_set", "mc_table_bytes",
 ]
 
 
@@ -133,6 +135,7 @@ def load(path: str | None = None):
         lib.mc_tables_status.argtypes = [P, P]
         lib.mc_sample_stars.argtypes = [P, C.c_int, u64, u64, i64, P, P, P, P]
         lib.mc_autotune.argtypes = [C.c_int, C.c_char_p]
+        lib.mc_table_bytes.argtypes = [P, C.POINTER(i64), C.POINTER(i64)]
         lib.mc_autotune_choice.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, i64, i64, i64]
         lib.mc_autotune_set.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, i64, i64, i64, C.c_int]
         _lib = lib
@@ -291,7 +294,7 @@ class Tables:
 
     def __init__(self, graph: Graph, colors, k: int, count_bits: int = 64, stream=None,
                  zero_root: bool = False, own_memory: bool = False, skip_round: bool = False,
-                 _handle=None):
+                 succinct: bool = False, varlen: bool = False, _handle=None):
         torch = _torch()
         if _handle is not None:  # built by batch()
             self.graph, self.k, self.bits, self._alloc, self.handle = graph, k, count_bits, \
@@ -304,12 +307,19 @@ class Tables:
         h = C.c_void_p()
         # own_memory: the library allocates (stream-ordered scratch, no
         # callbacks into Python), e.g. for tables served from worker threads
-        flags = (MC_BUILD_ZERO_ROOT if zero_root else 0) | (MC_BUILD_SKIP_ROUND if skip_round else 0)
+        flags = (MC_BUILD_ZERO_ROOT if zero_root else 0) | (MC_BUILD_SKIP_ROUND if skip_round else 0) | \
+            (MC_BUILD_SUCCINCT if succinct else 0) | (MC_BUILD_VARLEN if varlen else 0)
         _check(load().mc_build_tables(graph.handle, _ptr(colors) if graph.n else None, k,
                                       count_bits, flags,
                                       None if own_memory else C.byref(self._alloc.struct),
                                       _stream_ptr(stream), C.byref(h)))
         self.handle = h
+
+    def table_bytes(self) -> tuple[int, int]:
+        """mc_table_bytes: (dense bytes, stored bytes) of the c and S levels."""
+        d, st = C.c_int64(), C.c_int64()
+        _check(load().mc_table_bytes(self.handle, C.byref(d), C.byref(st)))
+        return d.value, st.value
 
     def nonzeros(self, h: int, which: int = 0, stream=None) -> int:
         """mc_table_nonzeros: non-zero entries of level h (0: c, 1: S)."""

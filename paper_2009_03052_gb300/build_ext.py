@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmotif.so")
-SOURCES = ["graph.cu", "build.cu", "sample.cu", "catalog.cpp", "serve.cu", "gather_u64_8.cu", "gather_u64_16.cu",
-           "gather_u128_16.cu"]
+SOURCES = ["graph.cu", "build.cu", "sample.cu", "catalog.cpp", "serve.cu", "packed.cu", "gather_u64_8.cu",
+           "gather_u64_16.cu", "gather_u128_16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(HERE, "..", "include")]

@@ -572,6 +572,10 @@ void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allo
 {
     const int64_t n = t->g->n;
     if (n == 0) return;
+    if (t->packed) {
+        launch_packed_row_totals(t, h, allow0, allow1, tot, err, s);
+        return;
+    }
     const int W = t->geo.Wc[h], R = shape_catalog().r[h];
     if (t->bits == 64)
         launch_row_totals_t<uint64_t>((const uint64_t *)t->c[h], n, W, R, allow0, allow1, tot, err, s);
@@ -927,7 +931,8 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         MC_REQUIRE(colors || g->n == 0, "colors is NULL");
         if (k < 2 || k > MAXK) throw Error(MC_E_UNSUPPORTED, "k must be in 2..8");
         MC_REQUIRE(count_bits == 64 || count_bits == 128, "count_bits must be 64 or 128");
-        MC_REQUIRE((flags & ~(MC_BUILD_ZERO_ROOT | MC_BUILD_SKIP_ROUND)) == 0, "unknown flags");
+        MC_REQUIRE((flags & ~(MC_BUILD_ZERO_ROOT | MC_BUILD_SKIP_ROUND | MC_BUILD_SUCCINCT | MC_BUILD_VARLEN)) == 0,
+                   "unknown flags");
         if (flags & MC_BUILD_SKIP_ROUND) {
             MC_REQUIRE(k >= 4, "round skipping needs k >= 4");
             MC_REQUIRE(!(flags & MC_BUILD_ZERO_ROOT), "round skipping and zero-rooting do not combine");
@@ -939,6 +944,8 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         t->bits = count_bits;
         t->zero_root = flags & MC_BUILD_ZERO_ROOT;
         t->skip_round = flags & MC_BUILD_SKIP_ROUND;
+        t->varlen = flags & MC_BUILD_VARLEN;
+        const bool pack = (flags & (MC_BUILD_SUCCINCT | MC_BUILD_VARLEN)) != 0;
         t->geo = make_geometry(k);
         t->arena.stream = s;
         if (alloc) { t->arena.alloc.a = *alloc; t->arena.alloc.custom = true; }
@@ -985,6 +992,10 @@ extern "C" mc_status mc_build_tables(const mc_graph *g, const uint8_t *colors, i
         t->bucket[k] = t->arena.get<uint32_t>((size_t)t->nbucket + 1);
         enqueue_build(t, colors, s, true);
         finish_build(t, s);
+        if (pack) {
+            pack_tables(t, s);
+            t->packed = true;
+        }
     });
     if (st != MC_OK) { delete t; return st; }
     *out = t;
@@ -996,6 +1007,7 @@ extern "C" mc_status mc_rebuild_tables(mc_tables *t, const uint8_t *colors, void
     return guarded([&] {
         MC_REQUIRE(t, "tables is NULL");
         MC_REQUIRE(colors || t->g->n == 0, "colors is NULL");
+        if (t->packed) throw Error(MC_E_UNSUPPORTED, "packed (succinct) tables cannot be rebuilt in place");
         std::lock_guard<std::mutex> lock(t->idx_mu);
         enqueue_build(t, colors, (cudaStream_t)stream, false);
         t->stale = true;
@@ -1262,6 +1274,16 @@ extern "C" mc_status mc_table_nonzeros(const mc_tables *t, int h, int which, int
         if (which == 0 && h == 1) { *count = n; return; }
         const int64_t m = n * (which ? t->geo.Ws[h] : t->geo.Wc[h]);
         cudaStream_t s = (cudaStream_t)stream;
+        if (t->packed) {  // the packed level holds exactly its non-zero entries
+            int64_t c = 0;
+            if (n) {
+                MC_CUDA(cudaMemcpyAsync(&c, (which ? t->ps : t->pc)[h].off + n, sizeof(int64_t),
+                                        cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaStreamSynchronize(s));
+            }
+            *count = c;
+            return;
+        }
         Arena scratch(true);
         scratch.alloc = t->arena.alloc;
         scratch.stream = s;
@@ -1313,6 +1335,18 @@ extern "C" mc_status mc_read_table(const mc_tables *t, int h, int which, void *d
             } else {
                 std::memset(dst, 0, bytes);
                 for (int64_t v = 0; v < t->g->n; ++v) ((uint8_t *)dst)[v * (t->bits / 8)] = 1;
+            }
+        } else if (t->packed) {
+            if (dst_on_device) {
+                launch_unpack(t, h, which, dst, s);
+            } else {
+                Arena scratch(true);
+                scratch.alloc = t->arena.alloc;
+                scratch.stream = s;
+                void *tmp = scratch.get<uint8_t>(bytes);
+                launch_unpack(t, h, which, tmp, s);
+                MC_CUDA(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaStreamSynchronize(s));
             }
         } else {
             const void *src = which ? t->S[h] : t->c[h];

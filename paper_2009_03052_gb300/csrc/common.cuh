@@ -212,4 +212,48 @@ __host__ __device__ __forceinline__ unsigned insert_colour_gap(unsigned rel, int
     return (rel & ((1u << c) - 1u)) | ((rel >> c) << (c + 1));
 }
 
+// ---------------------------------------------------------------------------
+// Packed (zero-suppressed) table levels, Section 3.2.1: per node row only the
+// non-zero entries, in row order, each as a key (the entry's index in the
+// dense row) and a count.  Counts are stored at `width` bytes each when
+// `wid` is NULL (the table's width), else at the row's own width wid[v]
+// (1, 2, 4, 8 or 16 bytes: the fewest that hold the row's largest count, the
+// variable-length counts of Section 3.3.3).  Row v's keys are
+// key[off[v] .. off[v+1]), its counts start at byte boff[v] (a multiple of 8).
+// ---------------------------------------------------------------------------
+struct PackedView {
+    const int64_t *off = nullptr;
+    const int64_t *boff = nullptr;
+    const uint8_t *wid = nullptr;
+    const uint16_t *key = nullptr;
+    const uint8_t *val = nullptr;
+    int width = 8;
+};
+
+__device__ __forceinline__ u128 packed_value(const uint8_t *q, int w)
+{
+    switch (w) {
+    case 1: return (u128)q[0];
+    case 2: return (u128)*(const uint16_t *)q;
+    case 4: return (u128)*(const uint32_t *)q;
+    case 8: return (u128)*(const uint64_t *)q;
+    default: return (u128)((const uint64_t *)q)[0] | ((u128)((const uint64_t *)q)[1] << 64);
+    }
+}
+
+// Entry idx of row v (0 when it is not stored), by binary search of the
+// row's keys.
+__device__ __forceinline__ u128 packed_get(const PackedView &p, int64_t v, int idx)
+{
+    const int64_t lo = p.off[v], hi = p.off[v + 1];
+    int64_t l = lo, r = hi;
+    while (l < r) {
+        const int64_t mid = (l + r) >> 1;
+        if ((int)p.key[mid] < idx) l = mid + 1; else r = mid;
+    }
+    if (l >= hi || (int)p.key[l] != idx) return 0;
+    const int w = p.wid ? (int)p.wid[v] : p.width;
+    return packed_value(p.val + p.boff[v] + (l - lo) * w, w);
+}
+
 }  // namespace mc

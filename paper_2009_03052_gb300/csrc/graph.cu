@@ -33,6 +33,17 @@ void Allocator::release(void *p, size_t bytes, cudaStream_t s) const
     else cudaFree(p);
 }
 
+void Arena::release(void *p)
+{
+    for (size_t i = 0; i < blocks.size(); ++i)
+        if (blocks[i].first == p) {
+            if (scratch && !alloc.custom) cudaFreeAsync(p, stream);
+            else alloc.release(p, blocks[i].second, stream);
+            blocks.erase(blocks.begin() + (long)i);
+            return;
+        }
+}
+
 void Arena::release_all()
 {
     for (auto &b : blocks) {

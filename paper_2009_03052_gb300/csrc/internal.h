@@ -71,6 +71,7 @@ struct Arena {
         return static_cast<T *>(p);
     }
     void release_all();
+    void release(void *p);  // one block, by its pointer
     ~Arena() { release_all(); }
 };
 
@@ -123,6 +124,13 @@ void ensure_level_index(const mc_tables *t, int h, cudaStream_t s);
 // the error flags back (synchronises s); throws if the rebuild failed.
 // force: re-read even without a rebuild through the API (a replayed graph).
 void refresh_tables(const mc_tables *t, cudaStream_t s, bool force = false);
+// Replace every dense c and S level of t by its packed form (synchronises s).
+void pack_tables(mc_tables *t, cudaStream_t s);
+// Per-node totals over the allowed shapes of packed level h of c.
+void launch_packed_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
+                              cudaStream_t s);
+// Expand packed level h (which = 0: c, 1: S) into a dense n x W table.
+void launch_unpack(const mc_tables *t, int h, int which, void *dst, cudaStream_t s);
 
 // Warp tasks of the neighbour-sum kernel: a node with more than HUB_CHUNK
 // neighbours is split into chunks of HUB_CHUNK consecutive neighbours whose
@@ -203,6 +211,11 @@ struct mc_tables {
     uint32_t *ccnt = nullptr;
     mc::u128 *scan_tmp = nullptr;
     mc::u128 *dev_D = nullptr;
+    // packed levels (MC_BUILD_SUCCINCT / MC_BUILD_VARLEN): the dense c[h] and
+    // S[h] are freed once packed; pc / ps hold the levels instead
+    bool packed = false, varlen = false;
+    mc::PackedView pc[mc::MAXK + 1], ps[mc::MAXK + 1];
+    int64_t dense_bytes = 0, stored_bytes = 0;  // of the c and S levels
     bool stale = false;                         // rebuilt since R[k], bucketD[k] were read back
     bool level_stale[mc::MAXK + 1] = {false};   // root index of level h from an older colouring
     std::string broken;                         // set when a rebuild failed its checks

@@ -300,6 +300,7 @@ struct SampleArgs {
     int64_t n;
     const void *c[MAXK + 1];
     const void *S[MAXK + 1];
+    PackedView pc[MAXK + 1], ps[MAXK + 1];  // the levels of packed (succinct) tables
     const void *Sp[MAXK + 1];   // per level: inclusive prefix of each hub's chunk sums
     const int32_t *node_chunk0; // first chunk of a hub, -1 for other nodes
     int Bc[MAXK + 1], Bs[MAXK + 1], Wc[MAXK + 1], Ws[MAXK + 1];
@@ -332,14 +333,28 @@ struct SampleSmem {
     uint8_t unrank[MAXK][36];
 };
 
-template <typename CT, typename V>
+// Entry idx of node x's level-h row of c or S: dense rows, or (PK) a binary
+// search of the packed row's keys.
+template <typename CT, bool PK>
+__device__ __forceinline__ CT c_at(const SampleArgs &a, int h, int64_t x, int idx)
+{
+    if constexpr (PK) return (CT)packed_get(a.pc[h], x, idx);
+    else return ((const CT *)a.c[h])[x * a.Wc[h] + idx];
+}
+template <typename CT, bool PK>
+__device__ __forceinline__ CT s_at(const SampleArgs &a, int h, int64_t x, int idx)
+{
+    if constexpr (PK) return (CT)packed_get(a.ps[h], x, idx);
+    else return ((const CT *)a.S[h])[x * a.Ws[h] + idx];
+}
+
+template <typename CT, typename V, bool PK>
 __device__ __forceinline__ V count_at(const SampleArgs &a, const SampleSmem &sm, int g, unsigned C, uint32_t x, int cx)
 {
     const int hg = a.sz[g];
     if (hg == 1) return 1;
     const unsigned rel = drop_colour(C & ~(1u << cx), cx);
-    const CT *row = (const CT *)a.c[hg] + (int64_t)x * a.Wc[hg];
-    return (V)row[sm.crank[rel] * a.R_[hg] + a.loc[g]];
+    return (V)c_at<CT, PK>(a, hg, x, sm.crank[rel] * a.R_[hg] + a.loc[g]);
 }
 
 __device__ __forceinline__ uint64_t quotient(uint64_t a, uint64_t b) { return a / b; }
@@ -429,7 +444,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 // running sums (64 bits when every level total leaves room for beta, else
 // 128 bits).
 
-template <typename CT, typename V>
+template <typename CT, typename V, bool PK>
 __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ SampleArgs a)
 {
     extern __shared__ unsigned int s_hist[];
@@ -474,7 +489,6 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
         unsigned C0 = 0;
         if (ok) {
             const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
-            const CT *vrow = (const CT *)a.c[h] + (int64_t)v * a.Wc[h];
             const int Bc = a.Bc[h], Rh = a.R_[h];
             V bf;
             // e runs in (shape id, colour mask) order; the row is set-major
@@ -482,7 +496,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
                 rb += al ? CB : 0;
-                return al ? (V)vrow[(e - sh * Bc) * Rh + sh] : (V)0;
+                return al ? (V)c_at<CT, PK>(a, h, v, (e - sh * Bc) * Rh + sh) : (V)0;
             }, bf);
             if (found < 0) { ok = false; bad = true; }
             else {
@@ -519,7 +533,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                 e0 = a.row_ptr[x];
                 e1 = a.row_ptr[x + 1];
                 chunk0 = a.node_chunk0[x];
-                const V W = (V)a.beta[g] * count_at<CT, V>(a, sm, g, C, x, cx);
+                const V W = (V)a.beta[g] * count_at<CT, V, PK>(a, sm, g, C, x, cx);
                 V Y = 0;
                 if (!draw_below(a.seed, index, step, W, Y)) { ok = false; bad = true; }
                 if (ok) {
@@ -528,21 +542,20 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                     const int nr = __popc(rest);
                     int nsub = 1;
                     for (int i = 1; i <= hb; ++i) nsub = nsub * (nr - hb + i) / i;
-                    const CT *srow = (const CT *)a.S[hb] + (int64_t)x * a.Ws[hb];
                     sbase = a.loc[gb];
                     const int Rb = a.R_[hb];
                     V before;
                     const int blk = lane_first_exceeding<V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
                         rb += 2 * CB;
-                        return count_at<CT, V>(a, sm, ga, C & ~c2, x, cx) *
-                               (V)srow[sm.crank[drop_colour(c2, cx)] * Rb + sbase];
+                        return count_at<CT, V, PK>(a, sm, ga, C & ~c2, x, cx) *
+                               (V)s_at<CT, PK>(a, hb, x, sm.crank[drop_colour(c2, cx)] * Rb + sbase);
                     }, before);
                     if (blk < 0) { ok = false; bad = true; }
                     else {
                         C2 = deposit(sm.unrank[hb][blk], rest);
                         C1 = C & ~C2;
-                        const V x1 = count_at<CT, V>(a, sm, ga, C1, x, cx);
+                        const V x1 = count_at<CT, V, PK>(a, sm, ga, C1, x, cx);
                         q = (CT)quotient(Y - before, x1);  // < S(T'', C'', x): fits CT
                         sidx = sm.crank[drop_colour(C2, cx)] * a.R_[hb] + sbase;
                         if (chunk0 >= 0) nch = (e1 - e0 + HUB_CHUNK - 1) / HUB_CHUNK;
@@ -601,8 +614,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                 int64_t sel = -1;
                 {
                     const int lb = a.loc[gb];
-                    const CT *chb = (const CT *)a.c[hb];
-                    const int rcb = a.R_[hb], wcb = a.Wc[hb];
+                    const int rcb = a.R_[hb];
                     CT bn;
                     const int r = lane_first_exceeding<CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
@@ -610,7 +622,7 @@ __global__ void __launch_bounds__(256, 6) sample_kernel(const __grid_constant__ 
                         if (!((C2 >> cu) & 1u)) return (CT)0;
                         rb += 4 + CB;
                         const uint32_t u = a.col[lo_e + i];
-                        return chb[(int64_t)u * wcb + sm.crank[drop_colour(C2 & ~(1u << cu), cu)] * rcb + lb];
+                        return c_at<CT, PK>(a, hb, u, sm.crank[drop_colour(C2 & ~(1u << cu), cu)] * rcb + lb);
                     }, bn);
                     if (r >= 0) sel = lo_e + r;
                 }
@@ -861,6 +873,8 @@ static void fill_sample_args(SampleArgs &a, const mc_tables *t, int h)
     for (int i = 1; i <= t->k; ++i) {
         a.c[i] = t->c[i];
         a.S[i] = t->S[i];
+        a.pc[i] = t->pc[i];
+        a.ps[i] = t->ps[i];
         a.Sp[i] = t->Sp[i];
         a.Bc[i] = t->geo.Bc[i];
         a.Bs[i] = t->geo.Bs[i];
@@ -971,8 +985,12 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     // most beta (<= 7) times a count of the level, every running sum at most
     // a level total
     const bool narrow = t->bits == 64 && ((a.R + a.Xbase) >> 61) == 0;
-    auto kern = t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t> : sample_kernel<uint64_t, u128>)
-                              : sample_kernel<u128, u128>;
+    auto kern = t->packed ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, true>
+                                                     : sample_kernel<uint64_t, u128, true>)
+                                           : sample_kernel<u128, u128, true>)
+                          : (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false>
+                                                     : sample_kernel<uint64_t, u128, false>)
+                                           : sample_kernel<u128, u128, false>);
     int per_sm = 0;
     MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
     if (per_sm < 1) per_sm = 1;
