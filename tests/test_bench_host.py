@@ -45,3 +45,16 @@ def test_gather_and_merge_bytes():
 def test_job_throughput_single_rank():
     ms, v = bench.job_throughput(1000.0, 2.0, 1)
     assert ms == 2.0 and v == 1000.0 / 0.002
+
+
+def test_traffic_only_for_the_captured_source(monkeypatch):
+    # an ncu traffic figure is reported while the kernel's source file hashes
+    # to the value recorded with the capture, and dropped once it changes
+    h = bench.source_hash("sample")
+    assert len(h) == 16
+    monkeypatch.setitem(bench.TRAFFIC, ("w", "sample"), (123, h))
+    assert bench.traffic_of("w", "sample") == 123
+    monkeypatch.setitem(bench.TRAFFIC, ("w", "sample"), (123, "0" * 16))
+    assert bench.traffic_of("w", "sample") is None
+    assert bench.traffic_of("w", "gather_h3") is None
+    assert bench.source_hash("gather_h3") == bench.source_hash("gather_h4") != ""

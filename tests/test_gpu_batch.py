@@ -74,3 +74,36 @@ def test_batch_equals_single_instances(M, oracle):
     oe, oh, ost = O.estimate_ags(k, seed=4, max_samples=100_000, cbar=100)
     assert np.array_equal(bh, oh)
     assert (st["samples"], st["switches"]) == (ost["samples"], ost["switches"])
+
+
+def test_union_rebuild_replayed_from_a_cuda_graph(M, oracle):
+    """The whole batch rebuilt in place for new colourings of every instance:
+    one captured CUDA graph of mc_rebuild_tables on the union, replayed; each
+    instance's rows then equal a fresh single build with its new colouring."""
+    import torch
+    k, bits = 6, 128
+    inst = _instances(oracle, k)
+    graphs = [M.Graph.from_csr(g) for g, _ in inst]
+    TB, offs = M.Tables.batch(graphs, [c for _, c in inst], k, bits)
+    buf = torch.empty(int(offs[-1]), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(s)
+    with torch.cuda.stream(side):
+        TB.rebuild(torch.cat([torch.as_tensor(c).cuda() for _, c in inst]))
+    s.wait_stream(side)
+    TB.status()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        TB.rebuild(buf)
+    for rnd in range(2):
+        new = [oracle.color(g.n, k, 900 + 10 * rnd + i) for i, (g, _) in enumerate(inst)]
+        buf.copy_(torch.cat([torch.as_tensor(c) for c in new]).cuda())
+        graph.replay()
+        TB.status()
+        for i, (G, c) in enumerate(zip(graphs, new)):
+            lo, hi = int(offs[i]), int(offs[i + 1])
+            T = M.Tables(G, c, k, bits)
+            for h in (2, 4, k):
+                assert np.array_equal(TB.read(h, 0)[lo:hi], T.read(h, 0)), (rnd, i, h)
+            assert TB.total(k, node_range=(lo, hi)) == T.total(k)
