@@ -378,18 +378,17 @@ __device__ __forceinline__ unsigned deposit(unsigned im, unsigned rest)
 
 // Per-lane search: over items 0 .. len-1 in order, the first whose running
 // sum of val(i) exceeds q (-1 if none), `before` the running sum before it.
-// Items are loaded four at a time so that their loads are in flight
-// together.
-template <typename V, typename F>
+// Items are loaded NW at a time so that their loads are in flight together.
+template <int NW, typename V, typename F>
 __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &before)
 {
     V run = 0;
-    for (int b = 0; b < len; b += 4) {
-        V v[4];
+    for (int b = 0; b < len; b += NW) {
+        V v[NW];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = b + i < len ? val(b + i) : (V)0;
+        for (int i = 0; i < NW; ++i) v[i] = b + i < len ? val(b + i) : (V)0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NW; ++i) {
             if (b + i < len && run + v[i] > q) { before = run; return b + i; }
             run += v[i];
         }
@@ -397,15 +396,16 @@ __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &befo
     return -1;
 }
 
-// Up to four adjacency tests at once (binary search of the shorter list),
+// Up to NQ adjacency tests at once (binary search of the shorter list),
 // advancing all searches one level per round so their loads overlap.
+template <int NQ = 4>
 __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t *col, const uint32_t *qa,
                                           const uint32_t *qb, int nq, bool *out, uint64_t &rb)
 {
-    int64_t lo[4], hi[4], end[4];
-    uint32_t key[4];
+    int64_t lo[NQ], hi[NQ], end[NQ];
+    uint32_t key[NQ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NQ; ++i) {
         if (i < nq) {
             uint32_t x = qa[i], y = qb[i];
             const int64_t dx = row_ptr[x + 1] - row_ptr[x], dy = row_ptr[y + 1] - row_ptr[y];
@@ -424,7 +424,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
     while (more) {
         more = false;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < NQ; ++i)
             if (lo[i] < hi[i]) {
                 const int64_t mid = (lo[i] + hi[i]) >> 1;
                 if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
@@ -433,7 +433,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = i < nq && lo[i] < end[i] && col[lo[i]] == key[i];
+    for (int i = 0; i < NQ; ++i) out[i] = i < nq && lo[i] < end[i] && col[lo[i]] == key[i];
 }
 
 // Lane-per-sample sampler: the 32 lanes of a warp draw 32 samples and walk
@@ -446,9 +446,16 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 
 // Occupancy target: 6 blocks of 256 per SM for 64-bit counts, 4 for 128-bit
 // ones (their wider state spills less; measured faster on both workloads).
-template <typename CT, typename V, bool PK>
-__global__ void __launch_bounds__(256, sizeof(CT) == 16 ? 4 : 6) sample_kernel(const __grid_constant__ SampleArgs a)
+// LAT (launches too small to fill the GPU, e.g. the batches of AGS): no
+// register cap, 16 items of a scan and 8 adjacency searches in flight per
+// lane, so each sample's chain of dependent loads is shorter.  The samples
+// are the same in both modes.
+template <typename CT, typename V, bool PK, bool LAT>
+__global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
+    sample_kernel(const __grid_constant__ SampleArgs a)
 {
+    constexpr int NW = LAT ? 16 : 4;  // items of a scan in flight
+    constexpr int NQ = LAT ? 8 : 4;   // adjacency searches in flight
     extern __shared__ unsigned int s_hist[];
     __shared__ SampleSmem sm;
     for (int i = threadIdx.x; i < (1 << (MAXK - 1)); i += blockDim.x) sm.crank[i] = a.crank[i];
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(256, sizeof(CT) == 16 ? 4 : 6) sample_kernel(c
             const int Bc = a.Bc[h], Rh = a.R_[h];
             V bf;
             // e runs in (shape id, colour mask) order; the row is set-major
-            const int found = lane_first_exceeding<V>(a.Wc[h], rem, [&](int e) -> V {
+            const int found = lane_first_exceeding<NW, V>(a.Wc[h], rem, [&](int e) -> V {
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
                 rb += al ? CB : 0;
@@ -547,7 +554,7 @@ __global__ void __launch_bounds__(256, sizeof(CT) == 16 ? 4 : 6) sample_kernel(c
                     sbase = a.loc[gb];
                     const int Rb = a.R_[hb];
                     V before;
-                    const int blk = lane_first_exceeding<V>(nsub, Y, [&](int i) -> V {
+                    const int blk = lane_first_exceeding<NW, V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
                         rb += 2 * CB;
                         return count_at<CT, V, PK>(a, sm, ga, C & ~c2, x, cx) *
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(256, sizeof(CT) == 16 ? 4 : 6) sample_kernel(c
                     const int lb = a.loc[gb];
                     const int rcb = a.R_[hb];
                     CT bn;
-                    const int r = lane_first_exceeding<CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
+                    const int r = lane_first_exceeding<NW, CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
                         rb += 1;
                         if (!((C2 >> cu) & 1u)) return (CT)0;
@@ -662,24 +669,24 @@ __global__ void __launch_bounds__(256, sizeof(CT) == 16 ? 4 : 6) sample_kernel(c
                 known |= 1u << pair_pos(h, i, j);
             }
             word = known;
-            uint32_t qa[4], qb[4];
-            int qp[4], nq = 0;
+            uint32_t qa[NQ], qb[NQ];
+            int qp[NQ], nq = 0;
             for (int p = 0; p < P; ++p) {
                 const int i = a.pi[p], j = a.pj[p];
                 const int bit = pair_pos(h, i, j);
                 if ((known >> bit) & 1u) continue;
                 qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
-                if (nq == 4 || p == P - 1) {
-                    bool r4[4];
-                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                if (nq == NQ || p == P - 1) {
+                    bool r4[NQ];
+                    adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb);
                     for (int t = 0; t < nq; ++t)
                         if (r4[t]) word |= 1u << qp[t];
                     nq = 0;
                 }
             }
             if (nq) {
-                bool r4[4];
-                adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                bool r4[NQ];
+                adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb);
                 for (int t = 0; t < nq; ++t)
                     if (r4[t]) word |= 1u << qp[t];
             }
@@ -979,7 +986,10 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
 
 static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
 {
-    const int block = 256;
+    // a launch that leaves most SMs idle runs the latency mode (dense tables)
+    // in blocks of 64, spread over more SMs
+    const bool lat = !t->packed && a.count <= (int64_t)sm_count() * 256;
+    const int block = lat ? 64 : 256;
     const size_t smem = a.hist ? (size_t)a.ncls * sizeof(unsigned int) : 0;
     // one wave of resident blocks: the grid-stride loop then keeps every
     // warp busy until the samples run out
@@ -987,12 +997,15 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     // most beta (<= 7) times a count of the level, every running sum at most
     // a level total
     const bool narrow = t->bits == 64 && ((a.R + a.Xbase) >> 61) == 0;
-    auto kern = t->packed ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, true>
-                                                     : sample_kernel<uint64_t, u128, true>)
-                                           : sample_kernel<u128, u128, true>)
-                          : (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false>
-                                                     : sample_kernel<uint64_t, u128, false>)
-                                           : sample_kernel<u128, u128, false>);
+    auto kern = t->packed ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, true, false>
+                                                     : sample_kernel<uint64_t, u128, true, false>)
+                                           : sample_kernel<u128, u128, true, false>)
+              : lat ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, true>
+                                               : sample_kernel<uint64_t, u128, false, true>)
+                                     : sample_kernel<u128, u128, false, true>)
+                    : (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, false>
+                                               : sample_kernel<uint64_t, u128, false, false>)
+                                     : sample_kernel<u128, u128, false, false>);
     int per_sm = 0;
     MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
     if (per_sm < 1) per_sm = 1;

@@ -240,3 +240,25 @@ def test_degenerate_inputs(M, oracle):
         M.Tables(G, np.full(g.n, 7, np.uint8), 4, 64)
     with pytest.raises(M.MotifError):
         M.Tables(G, oracle.color(g.n, 9, 0), 9, 64)
+
+
+@pytest.mark.parametrize("k,bits", [(5, 64), (7, 128)])
+def test_small_and_large_launches_draw_the_same_samples(M, oracle, k, bits):
+    """A launch too small to fill the GPU runs the sampler's latency mode
+    (more loads in flight per lane, small blocks); a large one the throughput
+    mode.  Sample i is the same either way: 100k samples in one launch equal
+    the same indices drawn 4096 at a time, and the oracle's on a slice."""
+    g = synth.chung_lu(20000, 150000, 2.3, seed=12)
+    colors = oracle.color(g.n, k, 3)
+    G = M.Graph.from_csr(g)
+    T = M.Tables(G, colors, k, bits)
+    big = [x.cpu().numpy() for x in T.sample(k, 77, 1000, 100_000)]
+    for first in (1000, 1000 + 4096 * 7, 1000 + 95_000):
+        cnt = min(4096, 101_000 - first)
+        small = [x.cpu().numpy() for x in T.sample(k, 77, first, cnt)]
+        for a, b in zip(big, small):
+            assert np.array_equal(a[first - 1000:first - 1000 + cnt], b)
+    O = oracle.Tables(g, colors, k, bits)
+    on, orr, osh, ocl = O.sample(k, 77, 1000 + 50_000, 300)
+    assert np.array_equal(big[0][50_000:50_300].astype(np.uint32), on)
+    assert np.array_equal(big[3][50_000:50_300], ocl)
