@@ -306,7 +306,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     launches = M.launch_count() - launches0
     prof_b = M.profile_read(with_bytes=True)
-    prof = {k: v[:2] for k, v in prof_b.items()}
+    prof = {k: v[:2] for k, v in prof_b.items() if v[1] > 0}  # kernels (the byte counters have no launches)
     M.profile_enable(False)
     clk = clocks.stop()
     if world > 1:
@@ -334,7 +334,17 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         hbm_peak, peak_src = 6800.0, "fallback"
     def roofline(nm):
         ms, cnt, counted = prof_b[nm]
-        if counted > 0:
+        item = None
+        sectors = prof_b.get(nm + " sectors", (0, 0, 0))[2]
+        if sectors > 0:
+            # the sector model of the sampler's bytes: 32 B per random access
+            # (root-search probes, each scanned neighbour's row entry, chunk-
+            # and adjacency-search probes), contiguous runs by their bytes
+            by = sectors / cnt
+            src = ("counted by the kernel, 32-byte sector model: 32 B per random access, "
+                   "contiguous runs by their bytes")
+            item = int(counted / cnt)
+        elif counted > 0:
             by, src = counted / cnt, "counted by the kernel (data items read and written)"
         else:
             by = algorithmic_bytes(nm, n, nnz, k, BITS // 8)
@@ -347,6 +357,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                "traffic": traffic, "algorithmic_bytes": int(by),
                "bytes_model": src, "peak_source": peak_src, "avg_launch_ms": round(ms / cnt, 4)}
+        if item is not None:  # the bytes of the data items themselves
+            out["item_bytes"] = item
+            out["item_frac"] = round(item / (ms / cnt / 1e3) / 1e9 / hbm_peak, 4)
         if traffic:  # the DRAM bytes of the ncu capture over this run's launch time
             dram = traffic / (ms / cnt / 1e3) / 1e9
             out["dram_gbs"] = round(dram, 1)

@@ -160,6 +160,46 @@ __global__ void __launch_bounds__(256, MINB) merge_kernel(const __grid_constant_
     if (inexact) atomicOr(a.err, ERR_INEXACT);
 }
 
+// The same merge with a thread per node walking all W outputs of its row in
+// (shape, set) order: every lane of a warp runs the same output program at
+// the same time (no divergence; the program's loads are uniform), reading
+// its own node's rows.
+template <typename CT, int MINB>
+__global__ void __launch_bounds__(256, MINB) merge_node_kernel(const __grid_constant__ MergeArgs a)
+{
+    bool ovf = false, inexact = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.n; v += (int64_t)gridDim.x * blockDim.x) {
+        CT *row = (CT *)a.out + v * a.W;
+        const bool zero = a.zero_root_colors && a.zero_root_colors[v] != 0;
+        for (int sh = 0; sh < a.R; ++sh)
+            for (int rho = 0; rho < a.Bc; ++rho) {
+                const int o = rho * a.R + sh;
+                if (zero) { row[o] = 0; continue; }
+                const int info = a.info[o];
+                const int h1 = info & 15, h2 = (info >> 4) & 15, beta = (info >> 8) & 255, nt = info >> 16;
+                const uint32_t *term = a.terms + a.off[o];
+                const CT *B = (const CT *)a.S[h2] + v * a.Ws[h2];
+                CT sum = 0;
+                if (h1 == 1) {
+                    for (int i = 0; i < nt; ++i) ovf |= add_ovf(sum, B[term[i] >> 16]);
+                } else {
+                    const CT *A = (const CT *)a.c[h1] + v * a.Wc[h1];
+                    for (int i = 0; i < nt; ++i) {
+                        const uint32_t tm = term[i];
+                        CT p;
+                        ovf |= mul_ovf(A[tm & 0xffffu], B[tm >> 16], p);
+                        ovf |= add_ovf(sum, p);
+                    }
+                }
+                CT qt;
+                if (!exact_div(sum, a.div[beta], qt)) inexact = true;
+                row[o] = qt;
+            }
+    }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (inexact) atomicOr(a.err, ERR_INEXACT);
+}
+
 // ---------------------------------------------------------------------------
 // per-node totals of a level over a set of shapes, and an inclusive u128
 // prefix over the nodes (the cumulative counts of Section 3.2.1, taken over
@@ -643,17 +683,21 @@ template <typename CT> static bool launch_gather(GatherArgs &ga, int r, int h, i
     return launch_gather_ub<uint64_t, 8>(ga, h, cand, s);
 }
 
-// Merge candidates: occupancy targets of 1 (no register cap), 6 and 8
-// blocks of 256 threads per SM.
-constexpr int MERGE_CANDIDATES = 3;
+// Merge candidates: a thread per output entry with occupancy targets of 1
+// (no register cap), 6 and 8 blocks of 256 threads per SM; a thread per node
+// (all of its outputs) at 6 and 8 blocks per SM.
+constexpr int MERGE_CANDIDATES = 5;
 
 template <typename CT> static bool launch_merge(const MergeArgs &ma, int h, int cand, cudaStream_t s)
 {
     const int grid = grid_for(ma.n * ma.W, 256);
+    const int gnode = grid_for(ma.n, 256);
     switch (cand) {
     case 0: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 1><<<grid, 256, 0, s>>>(ma)); return true;
     case 1: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 6><<<grid, 256, 0, s>>>(ma)); return true;
     case 2: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 8><<<grid, 256, 0, s>>>(ma)); return true;
+    case 3: MC_LAUNCH(kMergeName[h], s, merge_node_kernel<CT, 6><<<gnode, 256, 0, s>>>(ma)); return true;
+    case 4: MC_LAUNCH(kMergeName[h], s, merge_node_kernel<CT, 8><<<gnode, 256, 0, s>>>(ma)); return true;
     default: return false;
     }
 }

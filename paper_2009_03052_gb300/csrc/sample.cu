@@ -400,7 +400,7 @@ __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &befo
 // advancing all searches one level per round so their loads overlap.
 template <int NQ = 4>
 __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t *col, const uint32_t *qa,
-                                          const uint32_t *qb, int nq, bool *out, uint64_t &rb)
+                                          const uint32_t *qb, int nq, bool *out, uint64_t &rb, uint64_t &rs)
 {
     int64_t lo[NQ], hi[NQ], end[NQ];
     uint32_t key[NQ];
@@ -415,6 +415,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             end[i] = hi[i];
             key[i] = y;
             rb += 32 + 4;  // both degrees, the final probe
+            rs += 64 + 32;
         } else {
             lo[i] = hi[i] = end[i] = 0;
             key[i] = 0;
@@ -429,6 +430,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
                 const int64_t mid = (lo[i] + hi[i]) >> 1;
                 if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
                 rb += 4;
+                rs += 32;
                 more |= lo[i] < hi[i];
             }
     }
@@ -470,6 +472,8 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     const int CB = (int)sizeof(CT);
     bool bad = false;
     uint64_t rb = 0;  // bytes of the data items this lane reads and writes
+    uint64_t rs = 0;  // the same accesses in 32-byte sectors: 32 bytes per random access,
+                      // contiguous runs by their bytes
     for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
         const int64_t sid = base + lane;
         const uint64_t index = a.first_index + (uint64_t)sid;
@@ -484,12 +488,15 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             const uint64_t bk = (uint64_t)(X / (V)a.D);
             int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
             rb += 8;
+            rs += 32;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
                 rb += 16;
+                rs += 32;
             }
             rb += 32;  // the check below and prefix[v - 1]
+            rs += 32;
             v = (uint32_t)lo;
             if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
         }
@@ -505,6 +512,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
                 rb += al ? CB : 0;
+                rs += al ? CB : 0;  // one contiguous row
                 return al ? (V)c_at<CT, PK>(a, h, v, (e - sh * Bc) * Rh + sh) : (V)0;
             }, bf);
             if (found < 0) { ok = false; bad = true; }
@@ -539,6 +547,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             if (ok) {
                 ga = a.lft[g]; gb = a.rgt[g]; hb = a.sz[gb];
                 rb += 16 + 4 + CB;  // row offsets, first chunk, c(T_C, x)
+                rs += 96;
                 e0 = a.row_ptr[x];
                 e1 = a.row_ptr[x + 1];
                 chunk0 = a.node_chunk0[x];
@@ -557,6 +566,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                     const int blk = lane_first_exceeding<NW, V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
                         rb += 2 * CB;
+                        rs += 64;
                         return count_at<CT, V, PK>(a, sm, ga, C & ~c2, x, cx) *
                                (V)s_at<CT, PK>(a, hb, x, sm.crank[drop_colour(c2, cx)] * Rb + sbase);
                     }, before);
@@ -591,8 +601,10 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                     const int64_t mid = (lo + hi) >> 1;
                     if (spp[mid] > q) hi = mid; else lo = mid + 1;
                     rb += CB;
+                    rs += 32;
                 }
                 rb += 2 * CB;
+                rs += 32;
                 if (spp[lo] > q) { ci = lo; bc = lo ? spp[lo - 1] : (CT)0; }
             }
             int64_t lo_e = e0, hi_e = e1;
@@ -612,6 +624,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 const int32_t b0 = a.coff[(int64_t)x * (a.k + 1) + col2];
                 const int32_t b1 = a.coff[(int64_t)x * (a.k + 1) + col2 + 1];
                 rb += 8 + 4;
+                rs += 64;
                 if ((uint64_t)q >= (uint64_t)(b1 - b0) || sp + 2 > MAXK || ne >= MAXK) { ok = false; bad = true; }
                 else {
                     const uint32_t u = a.scol[e0 + b0 + (int64_t)q];
@@ -628,8 +641,10 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                     const int r = lane_first_exceeding<NW, CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
                         rb += 1;
+                        rs += 1;  // contiguous edge colours
                         if (!((C2 >> cu) & 1u)) return (CT)0;
                         rb += 4 + CB;
+                        rs += 4 + 32;  // contiguous ids; the neighbour's row entry
                         const uint32_t u = a.col[lo_e + i];
                         return c_at<CT, PK>(a, hb, u, sm.crank[drop_colour(C2 & ~(1u << cu), cu)] * rcb + lb);
                     }, bn);
@@ -678,7 +693,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
                 if (nq == NQ || p == P - 1) {
                     bool r4[NQ];
-                    adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                    adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
                     for (int t = 0; t < nq; ++t)
                         if (r4[t]) word |= 1u << qp[t];
                     nq = 0;
@@ -686,17 +701,19 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             }
             if (nq) {
                 bool r4[NQ];
-                adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
                 for (int t = 0; t < nq; ++t)
                     if (r4[t]) word |= 1u << qp[t];
             }
             cls = a.lut[word];
             rb += 2;
+            rs += 32;
             if (cls == 0xffff) { cls = -1; bad = true; }
             if (a.nodes) for (int i = 0; i < h; ++i) a.nodes[sid * h + i] = nodes[i];
             if (a.roots) a.roots[sid] = v;
             if (a.shapes) a.shapes[sid] = s0;
             rb += (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
+            rs += (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
             if (a.hist && cls >= 0) atomicAdd(&s_hist[cls], 1u);
         }
         if (sid < a.count && a.classes) a.classes[sid] = cls;
@@ -704,8 +721,14 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     if (bad) atomicOr(a.err, SERR_SEARCH);
     if (a.bytes) {
 #pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) rb += __shfl_xor_sync(0xffffffffu, rb, d);
-        if (lane == 0) atomicAdd(a.bytes, (unsigned long long)rb);
+        for (int d = 16; d >= 1; d >>= 1) {
+            rb += __shfl_xor_sync(0xffffffffu, rb, d);
+            rs += __shfl_xor_sync(0xffffffffu, rs, d);
+        }
+        if (lane == 0) {
+            atomicAdd(a.bytes, (unsigned long long)rb);
+            atomicAdd(a.bytes + 1, (unsigned long long)rs);
+        }
     }
     if (a.hist) {
         __syncthreads();
@@ -836,21 +859,21 @@ __global__ void __launch_bounds__(256) star_kernel(const __grid_constant__ StarA
         // four searches in flight
         uint32_t word = 0, qa[4], qb[4];
         int qp[4], nq = 0;
-        uint64_t rb = 0;
+        uint64_t rb = 0, rs = 0;
         for (int x = 0; x < h; ++x)
             for (int y = x + 1; y < h; ++y) {
                 if (nd[x] == c || nd[y] == c) { word |= 1u << pair_pos(h, x, y); continue; }
                 qa[nq] = nd[x]; qb[nq] = nd[y]; qp[nq] = pair_pos(h, x, y); ++nq;
                 if (nq == 4) {
                     bool r4[4];
-                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+                    adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
                     for (int q = 0; q < nq; ++q) if (r4[q]) word |= 1u << qp[q];
                     nq = 0;
                 }
             }
         if (nq) {
             bool r4[4];
-            adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb);
+            adjacent4(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
             for (int q = 0; q < nq; ++q) if (r4[q]) word |= 1u << qp[q];
         }
         const int cls = a.lut[word];
@@ -1024,18 +1047,21 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
 static unsigned long long *sample_byte_counter(Arena &scratch, cudaStream_t s)
 {
     if (!prof_enabled()) return nullptr;
-    unsigned long long *c = scratch.get<unsigned long long>(1);
-    MC_CUDA(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
+    unsigned long long *c = scratch.get<unsigned long long>(2);
+    MC_CUDA(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), s));
     return c;
 }
 
+// The sampler's counts: "sample" the bytes of the data items, "sample
+// sectors" the same accesses at 32 bytes per random access.
 static void report_sample_bytes(const unsigned long long *c, cudaStream_t s)
 {
     if (!c) return;
-    unsigned long long v = 0;
-    MC_CUDA(cudaMemcpyAsync(&v, c, sizeof(v), cudaMemcpyDeviceToHost, s));
+    unsigned long long v[2] = {0, 0};
+    MC_CUDA(cudaMemcpyAsync(v, c, sizeof(v), cudaMemcpyDeviceToHost, s));
     MC_CUDA(cudaStreamSynchronize(s));
-    prof_add_bytes("sample", (int64_t)v);
+    prof_add_bytes("sample", (int64_t)v[0]);
+    prof_add_bytes("sample sectors", (int64_t)v[1]);
 }
 
 static double inv_colourful_prob(int k, int h)
@@ -1422,7 +1448,8 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         } else {
             // Algorithm AGS with batched speculative sampling: a batch of
             // samples is drawn from the current treelet T_j; the host replays
-            // it in order and cuts it at the first newly covered graphlet,
+            // it in order and cuts it where a newly covered graphlet moves the
+            // choice to another treelet (a choice that stays keeps the batch),
             // which makes the outcome identical to one sample at a time.
             int64_t cbar = p->cbar;
             if (cbar <= 0) {
@@ -1534,6 +1561,9 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                             const double val = acc / tjd[j];
                             if (best < 0 || val < bestv) { best = j; bestv = val; }
                         }
+                        // the same treelet again: the rest of the batch is
+                        // exactly what one-at-a-time sampling draws next
+                        if (best == cur) continue;
                         cur = best;
                         st.discarded += b - q - 1;
                         switched = true;
@@ -1543,9 +1573,13 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 if (p->batch > 0) {
                     B = p->batch;
                 } else {
+                    // up to the predicted next covering; a batch used to its
+                    // end (no treelet change) doubles, since a covering that
+                    // keeps the treelet costs nothing
                     const int64_t q = cur >= 0 ? predict(cur) : -1;
-                    if (q >= 0) B = std::min<int64_t>(std::max<int64_t>(q + q / 4 + 4096, 4096), bmax);
-                    else B = switched ? bmin : std::min(2 * B, bmax);
+                    int64_t want = q >= 0 ? std::max<int64_t>(q + q / 4 + 4096, 4096) : (switched ? bmin : 2 * B);
+                    if (!switched) want = std::max(want, 2 * B);
+                    B = std::min(want, bmax);
                 }
             }
             weights();
