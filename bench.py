@@ -136,7 +136,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "20", "-i", str(self.device)], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "10", "-i", str(self.device)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
@@ -305,10 +305,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         step_ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     launches = M.launch_count() - launches0
-    prof_b = M.profile_read(with_bytes=True)
-    prof = {k: v[:2] for k, v in prof_b.items() if v[1] > 0}  # kernels (the byte counters have no launches)
-    M.profile_enable(False)
+    prof = {k: v[:2] for k, v in M.profile_read().items() if v[1] > 0}
     clk = clocks.stop()
+    # the bytes each kernel counts, from the last timed step run once more
+    # with counting on (its own instantiation; samples are deterministic)
+    M.profile_reset()
+    M.profile_enable(True, count_bytes=True)
+    step(seed0 + args.warmup + args.steps - 1, False)
+    torch.cuda.synchronize()
+    counted = M.profile_read(with_bytes=True)
+    M.profile_enable(False)
     if world > 1:
         dist.barrier()
     entries = n * live_entries_per_node(k)
@@ -333,19 +339,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     else:
         hbm_peak, peak_src = 6800.0, "fallback"
     def roofline(nm):
-        ms, cnt, counted = prof_b[nm]
+        ms, cnt = prof[nm]
         item = None
-        sectors = prof_b.get(nm + " sectors", (0, 0, 0))[2]
-        if sectors > 0:
-            # the sector model of the sampler's bytes: 32 B per random access
-            # (root-search probes, each scanned neighbour's row entry, chunk-
-            # and adjacency-search probes), contiguous runs by their bytes
-            by = sectors / cnt
+        cms, ccnt, citems = counted.get(nm, (0.0, 0, 0))
+        sectors = counted.get(nm + " sectors", (0.0, 0, 0))[2]
+        if sectors > 0 and ccnt > 0:
+            # the sector model of the sampler's bytes (32 B per random access:
+            # root-search probes, each scanned neighbour's row entry, chunk-
+            # and adjacency-search probes; contiguous runs by their bytes),
+            # per launch of the counting step
+            by = sectors / ccnt
             src = ("counted by the kernel, 32-byte sector model: 32 B per random access, "
-                   "contiguous runs by their bytes")
-            item = int(counted / cnt)
-        elif counted > 0:
-            by, src = counted / cnt, "counted by the kernel (data items read and written)"
+                   "contiguous runs by their bytes (one extra counted step)")
+            item = int(citems / ccnt)
         else:
             by = algorithmic_bytes(nm, n, nnz, k, BITS // 8)
             src = "compulsory bytes (each row read once, written once, plus the CSR)"

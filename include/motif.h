@@ -438,12 +438,16 @@ mc_status mc_sigma(int h, int64_t *sigma_i, int64_t *sigma_ij);
 /* ------------------------------------------------------------------------ */
 /* Tracing                                                                   */
 /* ------------------------------------------------------------------------ */
-/* When enabled, every kernel the library launches is bracketed by CUDA
- * events recorded on its own stream.  mc_profile_read synchronises those
- * events and reports, per kernel name, the summed device time (ms), the
- * number of launches and the bytes of data items the kernel's algorithm
- * read and wrote, where the kernel counts them (the sampler does, item by
- * item, while profiling is on; 0 elsewhere): names are written NUL-separated
+/* on = 1: every kernel the library launches is bracketed by CUDA events
+ * recorded on its own stream.  on = 3: the same, and sampler launches that
+ * fill the GPU (dense tables) count the bytes they read and write -- under
+ * "sample" the bytes of the data items, under "sample sectors" the same
+ * accesses at 32 bytes per random access (contiguous runs by their bytes) --
+ * in an instantiation of their own that synchronises its stream after each
+ * launch (so on = 1 times the uncounted kernel).  on = 0: off.
+ * mc_profile_read synchronises the events and reports, per kernel name, the
+ * summed device time (ms), the number of launches and the counted bytes (0
+ * where nothing is counted): names are written NUL-separated
  * into `names`, at most `max` kernels, their number into *count; any output
  * array may be NULL.  mc_launch_count is the number of kernels launched since
  * the library was loaded, whether or not profiling is on.  Profiling state is

@@ -499,8 +499,10 @@ def sigma(h: int) -> tuple[np.ndarray, np.ndarray]:
 # tracing
 # ---------------------------------------------------------------------------
 
-def profile_enable(on: bool = True):
-    _check(load().mc_profile_enable(1 if on else 0))
+def profile_enable(on: bool = True, count_bytes: bool = False):
+    """mc_profile_enable: time every launch; count_bytes also has the
+    sampler count its bytes (items and 32-byte sectors)."""
+    _check(load().mc_profile_enable((3 if count_bytes else 1) if on else 0))
 
 
 def profile_reset():

@@ -1175,7 +1175,7 @@ static u128 level_rooted_total(const mc_tables *t, int h, int j, int64_t lo, int
 // Copies of unrooted shape j from its rooted total: R / h (one rooted copy
 // per node), R at a zero-rooted level k, R / a_j at a round-skipped level k
 // (a_j = 0: the star, not counted).
-static u128 unrooted_from_rooted(const mc_tables *t, int h, int j, u128 R)
+u128 mc::unrooted_from_rooted(const mc_tables *t, int h, int j, u128 R)
 {
     u128 div = (u128)t->copies_div(h);
     if (t->skip_round && h == t->k) {

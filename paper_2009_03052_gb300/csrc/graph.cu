@@ -213,7 +213,8 @@ __global__ void color_biased_kernel(int64_t n, int k, uint64_t seed, uint32_t L,
 namespace {
 struct ProfState {
     std::mutex mu;
-    bool on = false;
+    bool on = false;     // time every launch
+    bool count = false;  // the sampler counts its bytes (an instantiation of its own)
     std::vector<std::string> names;
     std::vector<double> ms;
     std::vector<int64_t> launches;
@@ -290,6 +291,7 @@ void prof_end(ProfSpan &span, cudaStream_t s)
 }
 
 bool prof_enabled() { return prof().on; }
+bool prof_counting() { return prof().on && prof().count; }
 
 void prof_add_bytes(const char *name, int64_t bytes)
 {
@@ -336,6 +338,7 @@ extern "C" mc_status mc_profile_enable(int on)
         ProfState &p = prof();
         std::lock_guard<std::mutex> lock(p.mu);
         p.on = on != 0;
+        p.count = (on & 2) != 0;
     });
 }
 

@@ -103,6 +103,7 @@ struct ProfSpan {
     int id = -1;
 };
 bool prof_enabled();
+bool prof_counting();
 void prof_add_bytes(const char *name, int64_t bytes);
 ProfSpan prof_begin(const char *name, cudaStream_t s);
 void prof_end(ProfSpan &span, cudaStream_t s);
@@ -124,6 +125,9 @@ void ensure_level_index(const mc_tables *t, int h, cudaStream_t s);
 // the error flags back (synchronises s); throws if the rebuild failed.
 // force: re-read even without a rebuild through the API (a replayed graph).
 void refresh_tables(const mc_tables *t, cudaStream_t s, bool force = false);
+// Copies of unrooted shape j from its rooted total R at level h: R / h, R at
+// a zero-rooted level k, R / a_j at a round-skipped level k (0 for the star).
+u128 unrooted_from_rooted(const mc_tables *t, int h, int j, u128 R);
 // Replace every dense c and S level of t by its packed form (synchronises s).
 void pack_tables(mc_tables *t, cudaStream_t s);
 // Per-node totals over the allowed shapes of packed level h of c.

@@ -396,9 +396,20 @@ __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &befo
     return -1;
 }
 
+// Byte counts of the sampler's accesses, compiled in only when CNT: rb the
+// bytes of the data items, rs the same accesses in 32-byte sectors (32 bytes
+// per random access, contiguous runs by their bytes).
+#define MC_COUNT(item, sector)           \
+    do {                                 \
+        if constexpr (CNT) {             \
+            rb += (uint64_t)(item);      \
+            rs += (uint64_t)(sector);    \
+        }                                \
+    } while (0)
+
 // Up to NQ adjacency tests at once (binary search of the shorter list),
 // advancing all searches one level per round so their loads overlap.
-template <int NQ = 4>
+template <int NQ = 4, bool CNT = false>
 __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t *col, const uint32_t *qa,
                                           const uint32_t *qb, int nq, bool *out, uint64_t &rb, uint64_t &rs)
 {
@@ -414,8 +425,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             hi[i] = row_ptr[x + 1];
             end[i] = hi[i];
             key[i] = y;
-            rb += 32 + 4;  // both degrees, the final probe
-            rs += 64 + 32;
+            MC_COUNT(32 + 4, 64 + 32);  // both degrees, the final probe
         } else {
             lo[i] = hi[i] = end[i] = 0;
             key[i] = 0;
@@ -429,8 +439,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
             if (lo[i] < hi[i]) {
                 const int64_t mid = (lo[i] + hi[i]) >> 1;
                 if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
-                rb += 4;
-                rs += 32;
+                MC_COUNT(4, 32);
                 more |= lo[i] < hi[i];
             }
     }
@@ -452,7 +461,7 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
 // register cap, 16 items of a scan and 8 adjacency searches in flight per
 // lane, so each sample's chain of dependent loads is shorter.  The samples
 // are the same in both modes.
-template <typename CT, typename V, bool PK, bool LAT>
+template <typename CT, typename V, bool PK, bool LAT, bool CNT>
 __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     sample_kernel(const __grid_constant__ SampleArgs a)
 {
@@ -471,9 +480,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     const int h = a.h;
     const int CB = (int)sizeof(CT);
     bool bad = false;
-    uint64_t rb = 0;  // bytes of the data items this lane reads and writes
-    uint64_t rs = 0;  // the same accesses in 32-byte sectors: 32 bytes per random access,
-                      // contiguous runs by their bytes
+    uint64_t rb = 0, rs = 0;  // byte counts (CNT): data items, 32-byte sectors
     for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
         const int64_t sid = base + lane;
         const uint64_t index = a.first_index + (uint64_t)sid;
@@ -487,16 +494,13 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
         if (ok) {
             const uint64_t bk = (uint64_t)(X / (V)a.D);
             int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
-            rb += 8;
-            rs += 32;
+            MC_COUNT(8, 32);
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
-                rb += 16;
-                rs += 32;
+                MC_COUNT(16, 32);
             }
-            rb += 32;  // the check below and prefix[v - 1]
-            rs += 32;
+            MC_COUNT(32, 32);  // the check below and prefix[v - 1]
             v = (uint32_t)lo;
             if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
         }
@@ -511,8 +515,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             const int found = lane_first_exceeding<NW, V>(a.Wc[h], rem, [&](int e) -> V {
                 const int sh = e / Bc;
                 const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
-                rb += al ? CB : 0;
-                rs += al ? CB : 0;  // one contiguous row
+                MC_COUNT(al ? CB : 0, al ? CB : 0);  // one contiguous row
                 return al ? (V)c_at<CT, PK>(a, h, v, (e - sh * Bc) * Rh + sh) : (V)0;
             }, bf);
             if (found < 0) { ok = false; bad = true; }
@@ -546,8 +549,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             CT q = 0;
             if (ok) {
                 ga = a.lft[g]; gb = a.rgt[g]; hb = a.sz[gb];
-                rb += 16 + 4 + CB;  // row offsets, first chunk, c(T_C, x)
-                rs += 96;
+                MC_COUNT(16 + 4 + CB, 96);  // row offsets, first chunk, c(T_C, x)
                 e0 = a.row_ptr[x];
                 e1 = a.row_ptr[x + 1];
                 chunk0 = a.node_chunk0[x];
@@ -565,8 +567,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                     V before;
                     const int blk = lane_first_exceeding<NW, V>(nsub, Y, [&](int i) -> V {
                         const unsigned c2 = deposit(sm.unrank[hb][i], rest);
-                        rb += 2 * CB;
-                        rs += 64;
+                        MC_COUNT(2 * CB, 64);
                         return count_at<CT, V, PK>(a, sm, ga, C & ~c2, x, cx) *
                                (V)s_at<CT, PK>(a, hb, x, sm.crank[drop_colour(c2, cx)] * Rb + sbase);
                     }, before);
@@ -600,11 +601,9 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 while (lo < hi) {
                     const int64_t mid = (lo + hi) >> 1;
                     if (spp[mid] > q) hi = mid; else lo = mid + 1;
-                    rb += CB;
-                    rs += 32;
+                    MC_COUNT(CB, 32);
                 }
-                rb += 2 * CB;
-                rs += 32;
+                MC_COUNT(2 * CB, 32);
                 if (spp[lo] > q) { ci = lo; bc = lo ? spp[lo - 1] : (CT)0; }
             }
             int64_t lo_e = e0, hi_e = e1;
@@ -623,8 +622,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 const int col2 = __ffs(C2) - 1;
                 const int32_t b0 = a.coff[(int64_t)x * (a.k + 1) + col2];
                 const int32_t b1 = a.coff[(int64_t)x * (a.k + 1) + col2 + 1];
-                rb += 8 + 4;
-                rs += 64;
+                MC_COUNT(8 + 4, 64);
                 if ((uint64_t)q >= (uint64_t)(b1 - b0) || sp + 2 > MAXK || ne >= MAXK) { ok = false; bad = true; }
                 else {
                     const uint32_t u = a.scol[e0 + b0 + (int64_t)q];
@@ -640,11 +638,9 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                     CT bn;
                     const int r = lane_first_exceeding<NW, CT>((int)(hi_e - lo_e), qq, [&](int i) -> CT {
                         const int cu = a.ecol[lo_e + i];
-                        rb += 1;
-                        rs += 1;  // contiguous edge colours
+                        MC_COUNT(1, 1);  // contiguous edge colours
                         if (!((C2 >> cu) & 1u)) return (CT)0;
-                        rb += 4 + CB;
-                        rs += 4 + 32;  // contiguous ids; the neighbour's row entry
+                        MC_COUNT(4 + CB, 4 + 32);  // contiguous ids; the neighbour's row entry
                         const uint32_t u = a.col[lo_e + i];
                         return c_at<CT, PK>(a, hb, u, sm.crank[drop_colour(C2 & ~(1u << cu), cu)] * rcb + lb);
                     }, bn);
@@ -693,7 +689,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
                 if (nq == NQ || p == P - 1) {
                     bool r4[NQ];
-                    adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
+                    adjacent4<NQ, CNT>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
                     for (int t = 0; t < nq; ++t)
                         if (r4[t]) word |= 1u << qp[t];
                     nq = 0;
@@ -701,25 +697,26 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             }
             if (nq) {
                 bool r4[NQ];
-                adjacent4<NQ>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
+                adjacent4<NQ, CNT>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
                 for (int t = 0; t < nq; ++t)
                     if (r4[t]) word |= 1u << qp[t];
             }
             cls = a.lut[word];
-            rb += 2;
-            rs += 32;
+            MC_COUNT(2, 32);
             if (cls == 0xffff) { cls = -1; bad = true; }
             if (a.nodes) for (int i = 0; i < h; ++i) a.nodes[sid * h + i] = nodes[i];
             if (a.roots) a.roots[sid] = v;
             if (a.shapes) a.shapes[sid] = s0;
-            rb += (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
-            rs += (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
+            {
+                const int ob = (a.nodes ? 4 * h : 0) + (a.roots ? 4 : 0) + (a.shapes ? 4 : 0) + (a.classes ? 4 : 0);
+                MC_COUNT(ob, ob);
+            }
             if (a.hist && cls >= 0) atomicAdd(&s_hist[cls], 1u);
         }
         if (sid < a.count && a.classes) a.classes[sid] = cls;
     }
     if (bad) atomicOr(a.err, SERR_SEARCH);
-    if (a.bytes) {
+    if (CNT && a.bytes) {
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
             rb += __shfl_xor_sync(0xffffffffu, rb, d);
@@ -1020,15 +1017,22 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     // most beta (<= 7) times a count of the level, every running sum at most
     // a level total
     const bool narrow = t->bits == 64 && ((a.R + a.Xbase) >> 61) == 0;
-    auto kern = t->packed ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, true, false>
-                                                     : sample_kernel<uint64_t, u128, true, false>)
-                                           : sample_kernel<u128, u128, true, false>)
-              : lat ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, true>
-                                               : sample_kernel<uint64_t, u128, false, true>)
-                                     : sample_kernel<u128, u128, false, true>)
-                    : (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, false>
-                                               : sample_kernel<uint64_t, u128, false, false>)
-                                     : sample_kernel<u128, u128, false, false>);
+    // byte counting (profiling) runs its own instantiation of the dense,
+    // throughput-mode kernel, so uncounted launches carry none of its work
+    const bool cnt = a.bytes != nullptr && !t->packed && !lat;
+    if (!cnt) a.bytes = nullptr;
+    auto kern = t->packed ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, true, false, false>
+                                                     : sample_kernel<uint64_t, u128, true, false, false>)
+                                           : sample_kernel<u128, u128, true, false, false>)
+              : lat ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, true, false>
+                                               : sample_kernel<uint64_t, u128, false, true, false>)
+                                     : sample_kernel<u128, u128, false, true, false>)
+              : cnt ? (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, false, true>
+                                               : sample_kernel<uint64_t, u128, false, false, true>)
+                                     : sample_kernel<u128, u128, false, false, true>)
+                    : (t->bits == 64 ? (narrow ? sample_kernel<uint64_t, uint64_t, false, false, false>
+                                               : sample_kernel<uint64_t, u128, false, false, false>)
+                                     : sample_kernel<u128, u128, false, false, false>);
     int per_sm = 0;
     MC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1046,7 +1050,7 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
 // to the profile after the launch (one more synchronisation).
 static unsigned long long *sample_byte_counter(Arena &scratch, cudaStream_t s)
 {
-    if (!prof_enabled()) return nullptr;
+    if (!prof_counting()) return nullptr;
     unsigned long long *c = scratch.get<unsigned long long>(2);
     MC_CUDA(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), s));
     return c;
@@ -1461,11 +1465,11 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             std::vector<double> tjd(nu);
             std::vector<RootIndex> ris(nu);
             std::vector<std::pair<uint64_t, uint64_t>> allows(nu);
+            // every treelet's root index once: its rooted total gives t_j
             for (int j = 0; j < nu; ++j) {
-                uint64_t rooted[2], un[2];
-                mc_status s2 = mc_total_range(t, h, j, p->node_lo, p->node_hi, rooted, un, stream);
-                if (s2 != MC_OK) throw Error(s2, "AGS: treelet totals failed");
-                tj[j] = (u128)un[0] | ((u128)un[1] << 64);
+                ris[j] = root_index(t, h, j, scratch, err + 1, s, allows[j].first, allows[j].second, p->node_lo,
+                                    p->node_hi);
+                tj[j] = unrooted_from_rooted(t, h, j, ris[j].R);
                 tjd[j] = (double)tj[j];
             }
             int cur = -1;

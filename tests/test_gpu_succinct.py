@@ -87,3 +87,29 @@ def test_packed_tables(M, oracle, case):
         assert stored < dense
     with pytest.raises(M.MotifError):
         P.rebuild(M.color(G, k, 1))
+
+
+def test_packed_degenerate_inputs(M, oracle):
+    # no nodes; isolated nodes only (every level above 1 all zeros); a path
+    # (no 4-star, so some rows are empty); zero samples
+    G = M.Graph(np.zeros(1, np.int64), np.zeros(0, np.uint32))
+    T = M.Tables(G, np.zeros(0, np.uint8), 4, 64, succinct=True, varlen=True)
+    assert T.total(4) == (0, 0) and T.table_bytes()[1] == 0
+    g = synth.from_edges(50, [], [])
+    G = M.Graph.from_csr(g)
+    T = M.Tables(G, oracle.color(50, 3, 0), 3, 64, succinct=True)
+    assert T.total(3) == (0, 0) and T.total(1) == (50, 50)
+    assert T.nonzeros(2) == 0 and T.nonzeros(1, 1) == 0
+    assert not T.read(3, 0).any()
+    with pytest.raises(M.MotifError):
+        T.sample(3, 1, 0, 10)
+    g = synth.path(40)
+    colors = oracle.color(g.n, 4, 2)
+    G = M.Graph.from_csr(g)
+    P = M.Tables(G, colors, 4, 128, succinct=True, varlen=True)
+    D = M.Tables(G, colors, 4, 128)
+    for h in range(1, 5):
+        assert np.array_equal(P.read(h, 0), D.read(h, 0))
+    if D.total(4)[0] > 0:
+        _same_samples(P, D, 4, 5, 300)
+    P.sample(4, 1, 0, 0)
