@@ -328,6 +328,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     build_ms = statistics.mean(phase["build"])
     sample_ms = statistics.mean(phase["sample"])
 
+    # the schedules the autotuner chose for this workload's levels
+    gn, gnnz, gmaxd = G.info()
+    schedules = {}
+    for h in range(2, k + 1):
+        schedules[f"merge_h{h}"] = M.autotune_choice(1, k, BITS, h, gn, gnnz, gmaxd)
+        if h < k:
+            schedules[f"gather_h{h}"] = M.autotune_choice(0, k, BITS, h, gn, gnnz, gmaxd)
+
     # per-kernel shares and the roofline of the dominant kernel
     ktot = sum(v[0] for v in prof.values()) or 1.0
     kernels = {name: {"ms": round(ms, 4), "launches": cnt, "share": round(ms / ktot, 4)}
@@ -358,7 +366,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         if by is None:
             return None
         achieved = by / (ms / cnt / 1e3) / 1e9
-        traffic = traffic_of(wname, nm)
+        traffic = traffic_of(wname, nm, schedules.get(nm))
         out = {"kernel": nm, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                "traffic": traffic, "algorithmic_bytes": int(by),
@@ -417,13 +425,6 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                           f"and estimates ({r['sample_s']:.2f} s)"),
                "build_entries_per_s": r["build_entries_per_s"], "samples_per_s": r["samples_per_s"]}
 
-    # the schedules the autotuner chose for this workload's levels
-    gn, gnnz, gmaxd = G.info()
-    schedules = {}
-    for h in range(2, k + 1):
-        schedules[f"merge_h{h}"] = M.autotune_choice(1, k, BITS, h, gn, gnnz, gmaxd)
-        if h < k:
-            schedules[f"gather_h{h}"] = M.autotune_choice(0, k, BITS, h, gn, gnnz, gmaxd)
 
     extra = {}
     if rank == 0 and not args.no_extra and not args.small:
@@ -812,10 +813,10 @@ def run_serve(args):
 # profiles/), with a hash of the kernel's source file when it was captured:
 # the figure is reported only while that source is unchanged.
 TRAFFIC: dict = {
-    # profiles/gather_kernel_chung_lu_1m_k5.md (autotuned schedule 4 at every level)
-    ("chung_lu_1m_k5", "gather_h2"): (407_757_568, "887df3f50aaa2286"),
-    ("chung_lu_1m_k5", "gather_h3"): (1_255_241_216, "887df3f50aaa2286"),
-    ("chung_lu_1m_k5", "gather_h4"): (1_106_222_592, "887df3f50aaa2286"),
+    # profiles/gather_kernel_chung_lu_1m_k5.md, all three captured under schedule 4
+    ("chung_lu_1m_k5", "gather_h2"): (407_757_568, "887df3f50aaa2286", 4),
+    ("chung_lu_1m_k5", "gather_h3"): (1_255_241_216, "887df3f50aaa2286", 4),
+    ("chung_lu_1m_k5", "gather_h4"): (1_106_222_592, "887df3f50aaa2286", 4),
 }
 KERNEL_SOURCE = {"sample": "sample.cu", "gather": "gather.cuh", "merge": "build.cu"}
 
@@ -829,9 +830,13 @@ def source_hash(kernel: str) -> str:
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def traffic_of(workload: str, kernel: str):
+def traffic_of(workload: str, kernel: str, schedule: int | None = None):
+    """The captured DRAM bytes per launch, while the kernel's source and (if
+    recorded) the autotuned schedule are those of the capture; else None."""
     entry = TRAFFIC.get((workload, kernel))
     if not entry or entry[1] != source_hash(kernel):
+        return None
+    if len(entry) > 2 and schedule is not None and entry[2] != schedule:
         return None
     return entry[0]
 

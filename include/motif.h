@@ -214,7 +214,7 @@ mc_status mc_tables_status(const mc_tables *t, void *stream);
  *   choices now and append every new one to it; the MC_AUTOTUNE_CACHE
  *   environment variable does the same at the first build.  One line per key: kind k bits h logn logdeg loghub choice.
  * mc_autotune_choice: the schedule chosen so far for kernel kind (0 the
- * neighbour sums, schedules 0..4; 1 the merge, schedules 0..4) at level h
+ * neighbour sums, schedules 0..6; 1 the merge, schedules 0..5) at level h
  * of tables with k colours and count_bits counts on graphs of n nodes, nnz
  * adjacency entries and largest degree max_degree (mc_graph_info), or -1.
  * mc_autotune_set: fix that choice (MC_E_INVALID for an unknown kind or

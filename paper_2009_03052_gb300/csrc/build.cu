@@ -113,6 +113,7 @@ struct MergeArgs {
     void *out;
     int64_t n;
     int W, Bc, R;                     // row width, colour sets and shapes of the level
+    const MergeLevel *program;        // host copy of the program (schedule planning only)
     const uint8_t *zero_root_colors;  // set: only colour-0 nodes get counts
     int *err;
 };
@@ -156,6 +157,107 @@ __global__ void __launch_bounds__(256, MINB) merge_kernel(const __grid_constant_
         if (!exact_div(sum, a.div[beta], qt)) inexact = true;
         ((CT *)a.out)[v * a.W + o] = qt;
     }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (inexact) atomicOr(a.err, ERR_INEXACT);
+}
+
+// The merge with its operands streamed through shared memory: a block takes
+// tiles of NB consecutive nodes; while it computes the outputs of one tile
+// from one buffer, cp.async copies the next tile's rows (every lower level
+// the program reads; rows of consecutive nodes are contiguous) into the
+// other, 16 bytes per copy.  Waiting is cp.async.wait_group on the thread's
+// own copies, followed by a block barrier.
+struct MergeStage {
+    int nlev;
+    int is_s[2 * MAXK];
+    int lev[2 * MAXK];
+    int off[2 * MAXK];        // offset of the level's NB rows inside one buffer, in counts
+    int soff_c[MAXK + 1];     // the same per c level (-1: not staged)
+    int soff_s[MAXK + 1];
+    int NB;
+    int buf;                  // counts per buffer
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename CT>
+__device__ __forceinline__ void merge_stage_copy(const MergeArgs &a, const MergeStage &st, int64_t tile, CT *buf)
+{
+    const int64_t v0 = tile * st.NB;
+    if (v0 >= a.n) return;
+    const int nv = (int)min((int64_t)st.NB, a.n - v0);
+    for (int l = 0; l < st.nlev; ++l) {
+        const int h = st.lev[l];
+        const int W = st.is_s[l] ? a.Ws[h] : a.Wc[h];
+        const char *g = (const char *)((const CT *)(st.is_s[l] ? a.S[h] : a.c[h]) + v0 * W);
+        char *d = (char *)(buf + st.off[l]);
+        const int chunks = (int)(((int64_t)nv * W * (int64_t)sizeof(CT)) >> 4);
+        for (int i = threadIdx.x; i < chunks; i += blockDim.x) cp_async16(d + 16 * i, g + 16 * i);
+    }
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(256) merge_pipe_kernel(const __grid_constant__ MergeArgs a,
+                                                         const __grid_constant__ MergeStage st)
+{
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    CT *bufs = (CT *)s_raw;
+    bool ovf = false, inexact = false;
+    const int64_t ntiles = (a.n + st.NB - 1) / st.NB;
+    int64_t tile = blockIdx.x;
+    merge_stage_copy<CT>(a, st, tile, bufs);
+    cp_async_commit();
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        CT *cur = bufs + (int64_t)(it & 1) * st.buf;
+        merge_stage_copy<CT>(a, st, tile + gridDim.x, bufs + (int64_t)((it + 1) & 1) * st.buf);
+        cp_async_commit();
+        cp_async_wait1();   // this thread's copies of `tile` have landed
+        __syncthreads();    // and every other thread's
+        const int64_t v0 = tile * st.NB;
+        const int nv = (int)min((int64_t)st.NB, a.n - v0);
+        const int nout = nv * a.W;
+        for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+            const int vl = t / a.W;
+            const int q = t - vl * a.W;
+            const int sh = q / a.Bc;
+            const int o = (q - sh * a.Bc) * a.R + sh;
+            const int64_t v = v0 + vl;
+            CT *dst = (CT *)a.out + v * a.W + o;
+            if (a.zero_root_colors && a.zero_root_colors[v] != 0) {
+                *dst = 0;
+                continue;
+            }
+            const int info = a.info[o];
+            const int h1 = info & 15, h2 = (info >> 4) & 15, beta = (info >> 8) & 255, nt = info >> 16;
+            const uint32_t *term = a.terms + a.off[o];
+            CT sum = 0;
+            if (nt > 0) {
+                const CT *B = cur + st.soff_s[h2] + vl * a.Ws[h2];
+                if (h1 == 1) {
+                    for (int i = 0; i < nt; ++i) ovf |= add_ovf(sum, B[term[i] >> 16]);
+                } else {
+                    const CT *A = cur + st.soff_c[h1] + vl * a.Wc[h1];
+                    for (int i = 0; i < nt; ++i) {
+                        const uint32_t tm = term[i];
+                        CT p;
+                        ovf |= mul_ovf(A[tm & 0xffffu], B[tm >> 16], p);
+                        ovf |= add_ovf(sum, p);
+                    }
+                }
+            }
+            CT qt;
+            if (!exact_div(sum, a.div[beta], qt)) inexact = true;
+            *dst = qt;
+        }
+        __syncthreads();    // the buffer is free for the copy two tiles ahead
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     if (ovf) atomicOr(a.err, ERR_OVERFLOW);
     if (inexact) atomicOr(a.err, ERR_INEXACT);
 }
@@ -638,7 +740,10 @@ static int rows_in_flight(int NU) { return NU >= 16 ? 1 : NU >= 8 ? 2 : NU >= 4 
 //   1: R0 / 2,  2: R0 / 4 (fewer registers, more warps per SM)
 //   3: R0 / 2 with at most 40 registers (6 blocks of 256 per SM)
 //   4: R0 / 4 with at most 32 registers (8 blocks of 256 per SM)
-constexpr int GATHER_CANDIDATES = 5;
+//   5: one row in flight, 8 blocks per SM
+//   6: G0 / 2 lanes per node with two units each (twice the nodes per warp),
+//      a quarter of their rows in flight, 8 blocks per SM (2 <= G0 <= 16)
+constexpr int GATHER_CANDIDATES = 7;
 
 template <typename CT, int UB>
 static bool launch_gather_ub(const GatherArgs &ga, int h, int cand, cudaStream_t s)
@@ -656,6 +761,14 @@ static bool launch_gather_ub(const GatherArgs &ga, int h, int cand, cudaStream_t
     case 2: U = std::max(1, R0 / 4); break;
     case 3: U = std::max(1, R0 / 2); MB = 6; break;
     case 4: U = std::max(1, R0 / 4); MB = 8; break;
+    case 5: U = 1; MB = 8; break;
+    case 6:
+        if (G < 2 || G > 16) return false;
+        G /= 2;
+        NU *= 2;
+        U = std::max(1, rows_in_flight(NU) / 4);
+        MB = 8;
+        break;
     default: return false;
     }
     auto kern = gather_kernel_ptr(sizeof(CT), UB, G, NU, U, MB);
@@ -683,10 +796,50 @@ template <typename CT> static bool launch_gather(GatherArgs &ga, int r, int h, i
     return launch_gather_ub<uint64_t, 8>(ga, h, cand, s);
 }
 
+// The pipelined merge's staging plan for level h: the lower levels its
+// program reads, NB nodes per tile with two tiles of at most 96 KB of rows
+// per block; false when rows cannot be copied in 16-byte pieces.
+template <typename CT>
+static bool merge_stage_plan(const MergeArgs &ma, const MergeLevel &M, int h, MergeStage &st)
+{
+    bool use_c[MAXK + 1] = {false}, use_s[MAXK + 1] = {false};
+    for (int32_t info : M.info) {
+        if ((info >> 16) == 0) continue;
+        const int h1 = info & 15, h2 = (info >> 4) & 15;
+        if (h1 >= 2) use_c[h1] = true;
+        use_s[h2] = true;
+    }
+    int per_node = 0;
+    for (int x = 1; x < h; ++x) per_node += (use_c[x] ? ma.Wc[x] : 0) + (use_s[x] ? ma.Ws[x] : 0);
+    if (per_node == 0) return false;
+    const int cb = (int)sizeof(CT);
+    int NB = (int)std::min<int64_t>(64, (48 * 1024) / ((int64_t)per_node * cb));
+    if (cb == 8) NB &= ~1;  // u64 rows: an even count of rows per level is 16-byte aligned
+    if (NB < 1) return false;
+    st = MergeStage{};
+    st.NB = NB;
+    for (int x = 0; x <= MAXK; ++x) st.soff_c[x] = st.soff_s[x] = -1;
+    int off = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int x = 1; x < h; ++x) {
+            if (!(pass ? use_s[x] : use_c[x])) continue;
+            const int W = pass ? ma.Ws[x] : ma.Wc[x];
+            st.is_s[st.nlev] = pass;
+            st.lev[st.nlev] = x;
+            st.off[st.nlev] = off;
+            (pass ? st.soff_s : st.soff_c)[x] = off;
+            off += NB * W;
+            ++st.nlev;
+        }
+    st.buf = off;
+    return true;
+}
+
 // Merge candidates: a thread per output entry with occupancy targets of 1
 // (no register cap), 6 and 8 blocks of 256 threads per SM; a thread per node
-// (all of its outputs) at 6 and 8 blocks per SM.
-constexpr int MERGE_CANDIDATES = 5;
+// (all of its outputs) at 6 and 8 blocks per SM; the pipelined merge through
+// shared memory.
+constexpr int MERGE_CANDIDATES = 6;
 
 template <typename CT> static bool launch_merge(const MergeArgs &ma, int h, int cand, cudaStream_t s)
 {
@@ -698,6 +851,20 @@ template <typename CT> static bool launch_merge(const MergeArgs &ma, int h, int 
     case 2: MC_LAUNCH(kMergeName[h], s, merge_kernel<CT, 8><<<grid, 256, 0, s>>>(ma)); return true;
     case 3: MC_LAUNCH(kMergeName[h], s, merge_node_kernel<CT, 6><<<gnode, 256, 0, s>>>(ma)); return true;
     case 4: MC_LAUNCH(kMergeName[h], s, merge_node_kernel<CT, 8><<<gnode, 256, 0, s>>>(ma)); return true;
+    case 5: {
+        MergeStage st;
+        if (!ma.program || !merge_stage_plan<CT>(ma, *ma.program, h, st)) return false;
+        // the last partial tile of u64 rows may be an odd count: 16-byte
+        // copies need even tiles throughout
+        if (sizeof(CT) == 8 && (ma.n % st.NB) != 0 && ((ma.n % st.NB) & 1)) return false;
+        const size_t smem = 2 * (size_t)st.buf * sizeof(CT);
+        if (smem > 48 * 1024)
+            MC_CUDA(cudaFuncSetAttribute(merge_pipe_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t ntiles = (ma.n + st.NB - 1) / st.NB;
+        const int g = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * 4);
+        MC_LAUNCH(kMergeName[h], s, merge_pipe_kernel<CT><<<g, 256, smem, s>>>(ma, st));
+        return true;
+    }
     default: return false;
     }
 }
@@ -869,6 +1036,7 @@ template <typename CT> static void build_levels(mc_tables *t, int *err, cudaStre
         ma.W = G.Wc[h];
         ma.Bc = G.Bc[h];
         ma.R = shape_catalog().r[h];
+        ma.program = &programs(k, t->skip_round).merge[h];
         ma.zero_root_colors = (t->zero_root && h == k) ? t->colors : nullptr;
         const TuneKey mkey = tune_key(1, k, (int)sizeof(CT) * 8, h, n, g->nnz, g->max_degree);
         run_tuned(mkey, MERGE_CANDIDATES, allow_tune, s, [&](int c) { return launch_merge<CT>(ma, h, c, s); });

@@ -14,36 +14,43 @@ GatherKernel gather_kernel_ptr_u128_16(int G, int NU, int U, int MB)
     MC_G(1, 1, 2, 1)
     MC_G(1, 1, 4, 6)
     MC_G(1, 1, 2, 8)
+    MC_G(1, 1, 1, 8)
     MC_G(2, 1, 8, 1)
     MC_G(2, 1, 4, 1)
     MC_G(2, 1, 2, 1)
     MC_G(2, 1, 4, 6)
     MC_G(2, 1, 2, 8)
+    MC_G(2, 1, 1, 8)
     MC_G(4, 1, 8, 1)
     MC_G(4, 1, 4, 1)
     MC_G(4, 1, 2, 1)
     MC_G(4, 1, 4, 6)
     MC_G(4, 1, 2, 8)
+    MC_G(4, 1, 1, 8)
     MC_G(8, 1, 8, 1)
     MC_G(8, 1, 4, 1)
     MC_G(8, 1, 2, 1)
     MC_G(8, 1, 4, 6)
     MC_G(8, 1, 2, 8)
+    MC_G(8, 1, 1, 8)
     MC_G(16, 1, 8, 1)
     MC_G(16, 1, 4, 1)
     MC_G(16, 1, 2, 1)
     MC_G(16, 1, 4, 6)
     MC_G(16, 1, 2, 8)
+    MC_G(16, 1, 1, 8)
     MC_G(32, 1, 8, 1)
     MC_G(32, 1, 4, 1)
     MC_G(32, 1, 2, 1)
     MC_G(32, 1, 4, 6)
     MC_G(32, 1, 2, 8)
+    MC_G(32, 1, 1, 8)
     MC_G(32, 2, 8, 1)
     MC_G(32, 2, 4, 1)
     MC_G(32, 2, 2, 1)
     MC_G(32, 2, 4, 6)
     MC_G(32, 2, 2, 8)
+    MC_G(32, 2, 1, 8)
     MC_G(32, 4, 4, 1)
     MC_G(32, 4, 2, 1)
     MC_G(32, 4, 1, 1)
@@ -56,6 +63,10 @@ GatherKernel gather_kernel_ptr_u128_16(int G, int NU, int U, int MB)
     MC_G(32, 16, 1, 1)
     MC_G(32, 16, 1, 6)
     MC_G(32, 16, 1, 8)
+    MC_G(1, 2, 2, 8)
+    MC_G(2, 2, 2, 8)
+    MC_G(4, 2, 2, 8)
+    MC_G(8, 2, 2, 8)
 #undef MC_G
     return nullptr;
 }

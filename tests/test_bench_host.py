@@ -57,4 +57,7 @@ def test_traffic_only_for_the_captured_source(monkeypatch):
     monkeypatch.setitem(bench.TRAFFIC, ("w", "sample"), (123, "0" * 16))
     assert bench.traffic_of("w", "sample") is None
     assert bench.traffic_of("w", "gather_h3") is None
+    monkeypatch.setitem(bench.TRAFFIC, ("w", "gather_h3"), (7, bench.source_hash("gather_h3"), 4))
+    assert bench.traffic_of("w", "gather_h3", 4) == 7
+    assert bench.traffic_of("w", "gather_h3", 6) is None
     assert bench.source_hash("gather_h3") == bench.source_hash("gather_h4") != ""

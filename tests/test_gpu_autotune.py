@@ -1,6 +1,6 @@
 """Every schedule the autotuner can pick computes the same exact tables.
 
-Each neighbour-sum schedule (0..4) and each merge schedule (0..4) is pinned
+Each neighbour-sum schedule (0..6) and each merge schedule (0..5) is pinned
 in turn for every level of a build (mc_autotune_set, tuning off), and the
 tables must equal the oracle's bit for bit: at k = 5 with u64 counts (8- and
 16-byte units, 2 to 8 lanes per node) and k = 6 with u128 counts (up to 32
@@ -38,7 +38,7 @@ def test_every_schedule_builds_the_same_tables(M, oracle, k, bits, make):
     G = M.Graph.from_csr(g)
     n, nnz, maxd = G.info()
     M.autotune(0)  # pinned choices only
-    for gs, ms in [(0, 0), (1, 1), (2, 2), (3, 3), (4, 4)]:
+    for gs, ms in [(0, 0), (1, 1), (2, 2), (3, 3), (4, 4), (5, 5), (6, 0)]:
         for h in range(2, k + 1):
             M.autotune_set(1, k, bits, h, n, nnz, maxd, ms)
             if h < k:
@@ -64,6 +64,6 @@ def test_tuning_keeps_results(M, oracle):
     assert_tables_equal(M, T, O, g, colors, k)
     n, nnz, maxd = G.info()
     for h in range(2, k):
-        assert 0 <= M.autotune_choice(0, k, 64, h, n, nnz, maxd) < 5
+        assert 0 <= M.autotune_choice(0, k, 64, h, n, nnz, maxd) < 7
     for h in range(2, k + 1):
-        assert 0 <= M.autotune_choice(1, k, 64, h, n, nnz, maxd) < 5
+        assert 0 <= M.autotune_choice(1, k, 64, h, n, nnz, maxd) < 6

@@ -108,7 +108,7 @@ def test_autotune_choices_cache_file(motif, tmp_path):
     motif.autotune_set(0, 6, 128, 4, n, nnz, maxd, 2)
     assert motif.autotune_choice(0, 6, 128, 4, n, nnz, maxd) == 2
     with pytest.raises(motif.MotifError):
-        motif.autotune_set(1, 6, 128, 4, n, nnz, maxd, 5)   # the merge has schedules 0..4
+        motif.autotune_set(1, 6, 128, 4, n, nnz, maxd, 6)   # the merge has schedules 0..5
     with pytest.raises(motif.MotifError):
         motif.autotune(3)
     motif.autotune(1, "")
