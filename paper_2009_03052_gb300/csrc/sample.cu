@@ -396,6 +396,47 @@ __device__ __forceinline__ int lane_first_exceeding(int len, V q, F val, V &befo
     return -1;
 }
 
+// The first index i in [lo, hi) with pred(i) true, for a predicate that is
+// false then true along the range (hi if it is never true).  K = 1: binary
+// search; K > 1: K probes per round, evenly spaced, all loads in flight
+// together (about log_{K+1} of the range in dependent rounds).  on_probe()
+// runs once per evaluated probe.
+template <int K, typename P, typename F>
+__device__ __forceinline__ int64_t first_true(int64_t lo, int64_t hi, P pred, F on_probe)
+{
+    if constexpr (K == 1) {
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            on_probe();
+            if (pred(mid)) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    } else {
+        while (hi - lo > K) {
+            const int64_t step = (hi - lo) / (K + 1);
+            bool t[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) { t[i] = pred(lo + (i + 1) * step); on_probe(); }
+            int64_t nlo = lo + K * step + 1, nhi = hi;
+#pragma unroll
+            for (int i = K - 1; i >= 0; --i)
+                if (t[i]) { nhi = lo + (i + 1) * step; nlo = i ? lo + i * step + 1 : lo; }
+            lo = nlo;
+            hi = nhi;
+        }
+        bool t[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            t[i] = lo + i < hi ? pred(lo + i) : true;
+            if (lo + i < hi) on_probe();
+        }
+#pragma unroll
+        for (int i = K - 1; i >= 0; --i)
+            if (t[i]) hi = lo + i;
+        return hi;
+    }
+}
+
 // Byte counts of the sampler's accesses, compiled in only when CNT: rb the
 // bytes of the data items, rs the same accesses in 32-byte sectors (32 bytes
 // per random access, contiguous runs by their bytes).
@@ -467,6 +508,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
 {
     constexpr int NW = LAT ? 16 : 4;  // items of a scan in flight
     constexpr int NQ = LAT ? 8 : 4;   // adjacency searches in flight
+    constexpr int KS = LAT ? 8 : 1;   // probes per round of the root and hub chunk searches
     extern __shared__ unsigned int s_hist[];
     __shared__ SampleSmem sm;
     for (int i = threadIdx.x; i < (1 << (MAXK - 1)); i += blockDim.x) sm.crank[i] = a.crank[i];
@@ -493,13 +535,10 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
         X += (V)a.Xbase;  // a node range: the draw lands inside its part of the prefix
         if (ok) {
             const uint64_t bk = (uint64_t)(X / (V)a.D);
-            int64_t lo = a.bucket[bk], hi = a.bucket[bk + 1];
+            const int64_t blo = a.bucket[bk], bhi = a.bucket[bk + 1];
             MC_COUNT(8, 32);
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (a.prefix[mid] > (u128)X) hi = mid; else lo = mid + 1;
-                MC_COUNT(16, 32);
-            }
+            const int64_t lo = first_true<KS>(
+                blo, bhi, [&](int64_t i) { return a.prefix[i] > (u128)X; }, [&] { MC_COUNT(16, 32); });
             MC_COUNT(32, 32);  // the check below and prefix[v - 1]
             v = (uint32_t)lo;
             if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
@@ -597,12 +636,8 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             if (chunked) {
                 // the first chunk whose inclusive prefix exceeds q: a binary
                 // search of the hub's chunk prefix sums for this S entry
-                int64_t lo = 0, hi = nch - 1;
-                while (lo < hi) {
-                    const int64_t mid = (lo + hi) >> 1;
-                    if (spp[mid] > q) hi = mid; else lo = mid + 1;
-                    MC_COUNT(CB, 32);
-                }
+                const int64_t lo = first_true<KS>(
+                    0, nch - 1, [&](int64_t i) { return spp[i] > q; }, [&] { MC_COUNT(CB, 32); });
                 MC_COUNT(2 * CB, 32);
                 if (spp[lo] > q) { ci = lo; bc = lo ? spp[lo - 1] : (CT)0; }
             }
