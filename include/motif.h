@@ -294,11 +294,17 @@ typedef struct {
     int mode;              /* MC_EST_UNIFORM or MC_EST_AGS */
     int h;                 /* graphlet size, 2 <= h <= k */
     uint64_t seed;
-    uint64_t first_index;  /* index of the first sample */
-    int64_t samples;       /* uniform: samples drawn; AGS: the most it may draw */
+    uint64_t first_index;  /* uniform: sample s has index first_index + s; AGS: every
+                              treelet shape j has its own stream, the n-th sample drawn
+                              with T_j has index first_index + j * 2^40 + n */
+    int64_t samples;       /* uniform: samples drawn; AGS: the most it may draw (<= 2^40,
+                              else MC_E_INVALID) */
     int64_t cbar;          /* AGS covering threshold; <= 0: ceil(4/eps^2 ln(2s/delta)) */
     double eps, delta;     /* AGS accuracy, used when cbar <= 0 */
-    int64_t batch;         /* AGS speculative batch; <= 0: automatic */
+    int64_t batch;         /* AGS: samples drawn ahead for the current treelet per launch
+                              (and min(batch, 4096) for each other treelet whose drawn-ahead
+                              samples are used up); <= 0: automatic.  The result does not
+                              depend on it */
     int64_t node_lo, node_hi;  /* root nodes [node_lo, node_hi); node_hi <= 0: all nodes */
     uint32_t colour_bias_q32;  /* lambda_q32 of the biased colouring the tables were built with
                                   (0: uniform); the estimate divides by the probability
@@ -317,7 +323,7 @@ typedef struct {
     int64_t switches;   /* AGS: treelet switches */
     int64_t covered;    /* AGS: graphlets covered */
     int64_t batches;    /* device batches launched */
-    int64_t discarded;  /* AGS: speculative samples drawn and not used */
+    int64_t discarded;  /* AGS: samples drawn ahead and not used */
 } mc_estimate_stats;
 
 /* est: host double[N_h], the estimated number of induced copies of each

@@ -323,7 +323,8 @@ class Tables:
     def estimate_ags(self, h: int, seed: int, max_samples: int, cbar: int = 1000,
                      first_index: int = 0, star_samples: int = 0, bias_q32: int = 0,
                      trace: bool = False):
-        """(estimates, hits, stats).  trace=True adds to stats the first
+        """(estimates, hits, stats).  The n-th sample drawn with treelet
+        T_j has sample index first_index + j * 2^40 + n.  trace=True adds to stats the first
         treelet ("first") and, per switch, the treelet chosen ("trace_j"),
         the samples drawn by then ("trace_at") and the weights w it was
         chosen with ("trace_w", [switches, classes])."""

@@ -1074,8 +1074,11 @@ int oc_estimate_uniform(const oc_tables *t, int h, uint64_t seed, uint64_t first
  *    on a round-skipped level k the graphlets that only stars span
  *    (sigma'_i = 0) are left out of this and estimated from n_star
  *    uncoloured stars (star_estimates); the star shape has t_j = 0;
- *  - sample number s (0-based) uses sample index first_index + s, whatever
- *    treelet it draws from;
+ *  - every treelet has its own stream of sample indices: the n-th sample
+ *    (0-based) drawn with T_j uses index first_index + j * 2^40 + n, so
+ *    max_samples <= 2^40 (a reading: the paper does not say how random bits
+ *    are drawn; with one stream per treelet, samples drawn ahead for a
+ *    treelet stay valid whenever the algorithm comes back to it);
  *  - the result is est_i = (c_i / w_i) * (1/p), an estimate of the number
  *    of induced copies of H_i (c_i / w_i estimates its colourful copies);
  *    est_i = 0 when w_i = 0.
@@ -1091,7 +1094,8 @@ int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
                     double *est, uint64_t *hits, int64_t *stats,
                     int64_t trace_cap, int32_t *trace_j, int64_t *trace_at, double *trace_w)
 {
-    if (h < 2 || level_missing(t, h) || max_samples < 0 || cbar < 1) return OC_INVALID;
+    if (h < 2 || level_missing(t, h) || max_samples < 0 || max_samples > ((int64_t)1 << 40) || cbar < 1)
+        return OC_INVALID;
     int st = ensure_classes(h);
     if (st != OC_OK) return st;
     const int ncls = class_count[h];
@@ -1125,7 +1129,8 @@ int oc_estimate_ags(const oc_tables *t, int h, uint64_t seed, uint64_t first_ind
     int32_t shape;
     while (ncov < target && drawn < max_samples) {
         if (!ri[cur].prefix) { st = make_root_index(t, h, cur, &ri[cur]); if (st != OC_OK) goto done; }
-        st = sample_one(t, &ri[cur], seed, first_index + (uint64_t)drawn, nodes, &root, &shape);
+        st = sample_one(t, &ri[cur], seed, first_index + ((uint64_t)cur << 40) + (uint64_t)nj[cur], nodes, &root,
+                        &shape);
         if (st != OC_OK) goto done;
         nj[cur]++;
         drawn++;

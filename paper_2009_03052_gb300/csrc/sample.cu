@@ -290,6 +290,19 @@ ClassCatalog *class_catalog_sigma(int h)
 // The h leaves of the decomposition are the sample's nodes; their induced
 // subgraph is classified by the lookup table.
 // ---------------------------------------------------------------------------
+// One treelet's part of a launch that draws from several treelets: samples
+// [end of the previous part, end) come from this root index, the first with
+// sample index first_index.
+struct SampleSeg {
+    int64_t end;
+    uint64_t first_index;
+    const u128 *prefix;
+    const uint32_t *bucket;
+    u128 R, Xbase, D;
+    uint64_t allow0, allow1;
+};
+static_assert(sizeof(SampleSeg) <= 128, "request admission charges 128 bytes per part");
+
 struct SampleArgs {
     const int64_t *row_ptr;
     const uint32_t *col;
@@ -312,6 +325,8 @@ struct SampleArgs {
     const uint32_t *bucket;     // root-search buckets (nb + 1 entries)
     u128 D;                     // bucket width
     uint64_t allow0, allow1;
+    const SampleSeg *seg;       // nseg > 0: the launch's parts, each with its own root index and
+    int nseg;                   // index stream (prefix .. allow1 above unused)
     int first[MAXK + 2];
     uint8_t sz[MAX_SHAPES], loc[MAX_SHAPES], lft[MAX_SHAPES], rgt[MAX_SHAPES], beta[MAX_SHAPES];
     uint8_t crank[1 << (MAXK - 1)];        // colex rank of a set of the k-1 relative colours
@@ -525,35 +540,52 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     uint64_t rb = 0, rs = 0;  // byte counts (CNT): data items, 32-byte sectors
     for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
         const int64_t sid = base + lane;
-        const uint64_t index = a.first_index + (uint64_t)sid;
         bool ok = sid < a.count;
+        uint64_t index = a.first_index + (uint64_t)sid;
+        const u128 *prefix = a.prefix;
+        const uint32_t *bucket = a.bucket;
+        u128 R = a.R, Xbase = a.Xbase, D = a.D;
+        uint64_t allow0 = a.allow0, allow1 = a.allow1;
+        if (a.nseg > 0 && ok) {  // the part this sample falls in
+            int g = 0;
+            while (g + 1 < a.nseg && sid >= a.seg[g].end) ++g;
+            const SampleSeg &sg = a.seg[g];
+            index = sg.first_index + (uint64_t)(sid - (g ? a.seg[g - 1].end : 0));
+            prefix = sg.prefix;
+            bucket = sg.bucket;
+            R = sg.R;
+            Xbase = sg.Xbase;
+            D = sg.D;
+            allow0 = sg.allow0;
+            allow1 = sg.allow1;
+        }
         // ---- root: X = uniform(R); v = first node with prefix[v] > X, found
         // by binary search inside the bucket of X
         V X = 0;
         uint32_t v = 0;
-        if (ok && !draw_below(a.seed, index, 0, (V)a.R, X)) { ok = false; bad = true; }
-        X += (V)a.Xbase;  // a node range: the draw lands inside its part of the prefix
+        if (ok && !draw_below(a.seed, index, 0, (V)R, X)) { ok = false; bad = true; }
+        X += (V)Xbase;  // a node range: the draw lands inside its part of the prefix
         if (ok) {
-            const uint64_t bk = (uint64_t)(X / (V)a.D);
-            const int64_t blo = a.bucket[bk], bhi = a.bucket[bk + 1];
+            const uint64_t bk = (uint64_t)(X / (V)D);
+            const int64_t blo = bucket[bk], bhi = bucket[bk + 1];
             MC_COUNT(8, 32);
             const int64_t lo = first_true<KS>(
-                blo, bhi, [&](int64_t i) { return a.prefix[i] > (u128)X; }, [&] { MC_COUNT(16, 32); });
+                blo, bhi, [&](int64_t i) { return prefix[i] > (u128)X; }, [&] { MC_COUNT(16, 32); });
             MC_COUNT(32, 32);  // the check below and prefix[v - 1]
             v = (uint32_t)lo;
-            if (!(a.prefix[v] > (u128)X)) { ok = false; bad = true; }
+            if (!(prefix[v] > (u128)X)) { ok = false; bad = true; }
         }
         // ---- entry of v's level-h row, in (shape id, colour mask) order
         int s0 = 0, cv0 = 0;
         unsigned C0 = 0;
         if (ok) {
-            const V rem = X - (v ? (V)a.prefix[v - 1] : (V)0);
+            const V rem = X - (v ? (V)prefix[v - 1] : (V)0);
             const int Bc = a.Bc[h], Rh = a.R_[h];
             V bf;
             // e runs in (shape id, colour mask) order; the row is set-major
             const int found = lane_first_exceeding<NW, V>(a.Wc[h], rem, [&](int e) -> V {
                 const int sh = e / Bc;
-                const bool al = sh < 64 ? (a.allow0 >> sh) & 1 : (a.allow1 >> (sh - 64)) & 1;
+                const bool al = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
                 MC_COUNT(al ? CB : 0, al ? CB : 0);  // one contiguous row
                 return al ? (V)c_at<CT, PK>(a, h, v, (e - sh * Bc) * Rh + sh) : (V)0;
             }, bf);
@@ -1485,16 +1517,22 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             st.batches = 1;
             if (skipped) star_estimates(t, h, p, sig_prime, sig_star, est, hits, scratch, s);
         } else {
-            // Algorithm AGS with batched speculative sampling: a batch of
-            // samples is drawn from the current treelet T_j; the host replays
-            // it in order and cuts it where a newly covered graphlet moves the
-            // choice to another treelet (a choice that stays keeps the batch),
-            // which makes the outcome identical to one sample at a time.
+            // Algorithm AGS.  Every treelet T_j has its own stream of sample
+            // indices (the n-th sample drawn with T_j has index first_index +
+            // j * 2^40 + n), so samples can be drawn ahead: a refill launch
+            // draws a run for the current treelet and a short run for every
+            // other treelet whose queue is empty, and the host replays the
+            // algorithm one sample at a time, taking each from the queue of
+            // the treelet it has chosen, and comes back to the GPU only when
+            // that queue runs dry.  The outcome is the one of drawing one
+            // sample at a time; what is left in the queues at the end was
+            // drawn ahead and not used.
             int64_t cbar = p->cbar;
             if (cbar <= 0) {
                 MC_REQUIRE(p->eps > 0 && p->delta > 0 && p->delta < 1, "AGS needs cbar or (eps, delta)");
                 cbar = (int64_t)std::ceil(4.0 / (p->eps * p->eps) * std::log(2.0 * ncls / p->delta));
             }
+            MC_REQUIRE(p->samples <= ((int64_t)1 << 40), "AGS draws at most 2^40 samples");
             const int nu = cat.n_unrooted[h];
             std::vector<u128> tj(nu);
             std::vector<double> tjd(nu);
@@ -1515,11 +1553,19 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             std::vector<double> w((size_t)ncls, 0.0);
             std::vector<uint8_t> covered((size_t)ncls, 0);
             int64_t drawn = 0, ncov = 0;
+            // run lengths: the current treelet's first refill, its largest,
+            // and the short run drawn ahead for the others
             const int64_t bmin = p->batch > 0 ? p->batch : 65536;
-            int64_t B = bmin;
             const int64_t bmax = p->batch > 0 ? p->batch : (int64_t)1 << 22;
-            int32_t *dcls = scratch.get<int32_t>((size_t)bmax);
-            std::vector<int32_t> hcls((size_t)bmax);
+            const int64_t ahead = std::min<int64_t>(bmax, 4096);
+            const int64_t cap = bmax + (int64_t)nu * ahead;  // samples of one launch, at most
+            int32_t *dcls = scratch.get<int32_t>((size_t)cap);
+            SampleSeg *dseg = scratch.get<SampleSeg>((size_t)nu);
+            std::vector<int32_t> hcls((size_t)cap);
+            std::vector<SampleSeg> hseg((size_t)nu);
+            std::vector<std::vector<int32_t>> queue((size_t)nu);  // drawn, not yet used, in index order
+            std::vector<size_t> qpos((size_t)nu, 0);
+            std::vector<int64_t> queued(nu, 0), last(nu, 0);   // samples drawn with T_j; its last run
             auto weights = [&] {
                 for (int i = 0; i < ncls; ++i) {
                     double acc = 0.0;
@@ -1528,9 +1574,9 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     w[i] = acc;
                 }
             };
-            // Batch sizing only (the outcome does not depend on it): hits per
-            // class among the samples drawn with each T_j predict how many
-            // more samples T_j needs until some graphlet is covered.
+            // Run lengths only (the outcome does not depend on them): hits per
+            // class among the samples used from each T_j predict how many more
+            // T_j needs until some graphlet is covered.
             std::vector<uint64_t> hj((size_t)nu * ncls, 0);
             auto predict = [&](int j) -> int64_t {
                 if (nj[j] == 0) return -1;
@@ -1543,29 +1589,46 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 }
                 return best < 0.0 ? -1 : (int64_t)best;
             };
-            int64_t target = ncls;  // round-skipped: the graphlets only stars span are left to the stars
-            if (skipped) {
-                target = 0;
-                for (int i = 0; i < ncls; ++i) target += sig_prime[(size_t)i] > 0;
-            }
-            while (cur >= 0 && ncov < target && drawn < p->samples) {
-                if (!ris[cur].prefix) {
-                    ris[cur] = root_index(t, h, cur, scratch, err + 1, s, allows[cur].first, allows[cur].second,
-                                          p->node_lo, p->node_hi);
+            auto refill = [&] {
+                std::vector<int64_t> amount(nu, 0);
+                for (int j = 0; j < nu; ++j) {
+                    if (tj[j] == 0 || qpos[j] < queue[j].size()) continue;
+                    if (j == cur) {
+                        int64_t want = bmin;
+                        if (p->batch <= 0) {
+                            const int64_t q = predict(j);
+                            if (q >= 0) want = std::max<int64_t>(want, q + q / 4 + 4096);
+                            if (last[j] >= bmin) want = std::max(want, 2 * last[j]);  // its last run was used up
+                        }
+                        amount[j] = std::min(std::min(want, bmax), p->samples - drawn);
+                    } else {
+                        amount[j] = ahead;
+                    }
                 }
-                const int64_t b = std::min(B, p->samples - drawn);
+                int nseg = 0;
+                int64_t total = 0;
                 SampleArgs a;
                 fill_sample_args(a, t, h);
-                a.allow0 = allows[cur].first;
-                a.allow1 = allows[cur].second;
-                a.prefix = ris[cur].prefix;
-                a.R = ris[cur].R;
-                a.Xbase = ris[cur].base;
-                a.bucket = ris[cur].bucket;
-                a.D = ris[cur].D;
+                for (int j = 0; j < nu; ++j) {
+                    if (amount[j] <= 0) continue;
+                    SampleSeg &sg = hseg[(size_t)nseg++];
+                    total += amount[j];
+                    sg.end = total;
+                    sg.first_index = p->first_index + ((uint64_t)j << 40) + (uint64_t)queued[j];
+                    sg.prefix = ris[j].prefix;
+                    sg.bucket = ris[j].bucket;
+                    sg.R = ris[j].R;
+                    sg.Xbase = ris[j].base;
+                    sg.D = ris[j].D;
+                    sg.allow0 = allows[j].first;
+                    sg.allow1 = allows[j].second;
+                    if (ris[j].R + ris[j].base > a.R + a.Xbase) { a.R = ris[j].R; a.Xbase = ris[j].base; }  // for the width test
+                }
+                MC_CUDA(cudaMemcpyAsync(dseg, hseg.data(), (size_t)nseg * sizeof(SampleSeg), cudaMemcpyHostToDevice, s));
+                a.seg = dseg;
+                a.nseg = nseg;
                 a.seed = p->seed;
-                a.first_index = p->first_index + (uint64_t)drawn;
-                a.count = b;
+                a.count = total;
                 a.lut = cc->lut;
                 a.classes = dcls;
                 a.ncls = ncls;
@@ -1573,54 +1636,52 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.bytes = sample_byte_counter(scratch, s);
                 launch_sampler(t, a, s);
                 report_sample_bytes(a.bytes, s);
-                MC_CUDA(cudaMemcpyAsync(hcls.data(), dcls, (size_t)b * 4, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaMemcpyAsync(hcls.data(), dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
                 MC_CUDA(cudaStreamSynchronize(s));
                 st.batches++;
-                bool switched = false;
-                for (int64_t q = 0; q < b; ++q) {
-                    const int i = hcls[(size_t)q];
-                    if (i < 0 || i >= ncls) throw Error(MC_E_INTERNAL, "AGS: bad class id");
-                    nj[cur]++;
-                    drawn++;
-                    hv[(size_t)i]++;
-                    hj[(size_t)cur * ncls + i]++;
-                    if ((int64_t)hv[(size_t)i] == cbar && !covered[(size_t)i]) {
-                        covered[(size_t)i] = 1;
-                        ncov++;
-                        st.switches++;
-                        weights();
-                        int best = -1;
-                        double bestv = 0.0;
-                        for (int j = 0; j < nu; ++j) {
-                            if (tj[j] == 0) continue;
-                            double acc = 0.0;
-                            for (int a2 = 0; a2 < ncls; ++a2)
-                                if (covered[(size_t)a2])
-                                    acc += ((double)cc->sigma_ij[(size_t)a2 * nu + j] * (double)hv[(size_t)a2]) / w[(size_t)a2];
-                            const double val = acc / tjd[j];
-                            if (best < 0 || val < bestv) { best = j; bestv = val; }
-                        }
-                        // the same treelet again: the rest of the batch is
-                        // exactly what one-at-a-time sampling draws next
-                        if (best == cur) continue;
-                        cur = best;
-                        st.discarded += b - q - 1;
-                        switched = true;
-                        break;
-                    }
+                int64_t off = 0;
+                for (int j = 0; j < nu; ++j) {
+                    if (amount[j] <= 0) continue;
+                    queue[j].assign(hcls.begin() + off, hcls.begin() + off + amount[j]);
+                    qpos[j] = 0;
+                    queued[j] += amount[j];
+                    last[j] = amount[j];
+                    off += amount[j];
                 }
-                if (p->batch > 0) {
-                    B = p->batch;
-                } else {
-                    // up to the predicted next covering; a batch used to its
-                    // end (no treelet change) doubles, since a covering that
-                    // keeps the treelet costs nothing
-                    const int64_t q = cur >= 0 ? predict(cur) : -1;
-                    int64_t want = q >= 0 ? std::max<int64_t>(q + q / 4 + 4096, 4096) : (switched ? bmin : 2 * B);
-                    if (!switched) want = std::max(want, 2 * B);
-                    B = std::min(want, bmax);
+            };
+            int64_t target = ncls;  // round-skipped: the graphlets only stars span are left to the stars
+            if (skipped) {
+                target = 0;
+                for (int i = 0; i < ncls; ++i) target += sig_prime[(size_t)i] > 0;
+            }
+            while (cur >= 0 && ncov < target && drawn < p->samples) {
+                if (qpos[cur] == queue[cur].size()) refill();
+                const int i = queue[cur][qpos[cur]++];
+                if (i < 0 || i >= ncls) throw Error(MC_E_INTERNAL, "AGS: bad class id");
+                nj[cur]++;
+                drawn++;
+                hv[(size_t)i]++;
+                hj[(size_t)cur * ncls + i]++;
+                if ((int64_t)hv[(size_t)i] == cbar && !covered[(size_t)i]) {
+                    covered[(size_t)i] = 1;
+                    ncov++;
+                    st.switches++;
+                    weights();
+                    int best = -1;
+                    double bestv = 0.0;
+                    for (int j = 0; j < nu; ++j) {
+                        if (tj[j] == 0) continue;
+                        double acc = 0.0;
+                        for (int a2 = 0; a2 < ncls; ++a2)
+                            if (covered[(size_t)a2])
+                                acc += ((double)cc->sigma_ij[(size_t)a2 * nu + j] * (double)hv[(size_t)a2]) / w[(size_t)a2];
+                        const double val = acc / tjd[j];
+                        if (best < 0 || val < bestv) { best = j; bestv = val; }
+                    }
+                    cur = best;
                 }
             }
+            for (int j = 0; j < nu; ++j) st.discarded += (int64_t)(queue[j].size() - qpos[j]);
             weights();
             for (int i = 0; i < ncls; ++i) {
                 hits[i] = hv[(size_t)i];

@@ -80,10 +80,13 @@ static size_t request_memory(const mc_tables *t, const mc_request &r)
     if (!t->prefix[h]) m += index;
     if (p.mode == MC_EST_AGS) {
         // a root index per treelet shape it samples from (at most all of
-        // them), one shape-total pass, and the class ids of one batch
+        // them), one shape-total pass, and the class ids and part table of
+        // one launch (the current treelet's run and a short one per other)
         const int nu = mc_num_unrooted(h);
         const int64_t bmax = p.batch > 0 ? p.batch : (int64_t)1 << 22;
-        m += (size_t)std::max(nu, 1) * index + index + (size_t)bmax * 4;
+        const int64_t ahead = std::min<int64_t>(bmax, 4096);
+        m += (size_t)std::max(nu, 1) * index + index + (size_t)(bmax + (int64_t)nu * ahead) * 4 +
+             (size_t)nu * 128;
     }
     if (p.star_samples > 0 && !t->g->star_prefix[h]) m += index + cls;
     return m;

@@ -191,14 +191,18 @@ def test_ags_estimates(M, oracle):
     G = M.Graph.from_csr(g)
     T = M.Tables(G, colors, 4, 64)
     O = oracle.Tables(g, colors, 4, 64)
-    for batch in (0, 777):
+    # the run length per launch changes what is drawn ahead, never the result
+    for batch, first in ((0, 0), (777, 0), (5000, 123_456_789)):
         est, hits, st = T.estimate(4, seed=8, samples=300_000, mode=M.MC_EST_AGS, cbar=300,
-                                   batch=batch)
-        oest, ohits, ost = O.estimate_ags(4, seed=8, max_samples=300_000, cbar=300)
+                                   batch=batch, first_index=first)
+        oest, ohits, ost = O.estimate_ags(4, seed=8, max_samples=300_000, cbar=300, first_index=first)
         assert np.array_equal(hits, ohits)
         assert _ulp_close(est, oest)
         assert (st["samples"], st["switches"], st["covered"]) == \
             (ost["samples"], ost["switches"], ost["covered"])
+    # every treelet's index stream holds 2^40 samples
+    with pytest.raises(M.MotifError):
+        T.estimate(4, seed=8, samples=(1 << 40) + 1, mode=M.MC_EST_AGS, cbar=300)
 
 
 def test_overflow_is_reported(M, oracle):

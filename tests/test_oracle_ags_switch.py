@@ -10,8 +10,8 @@ in exact rational arithmetic from values it finds by brute force:
 * t_j: sum_i g_i sigma_ij with g_i the colourful induced copies of class i,
   found by listing node subsets (and checked against the oracle's totals);
 * the samples: drawn from the oracle's sampler, whose exact distribution is
-  pinned elsewhere, with the index stream of the algorithm (sample s of the
-  run has index first_index + s whatever treelet it comes from).
+  pinned elsewhere, with the index streams of the algorithm (the n-th sample
+  drawn with T_j has index first_index + j * 2^40 + n).
 
 The oracle's first treelet, the treelet chosen at every switch, the number
 of samples drawn by then and the weights w_i it used must equal the replay's.
@@ -66,7 +66,7 @@ def _replay(T, h, sig, t, seed, cbar, max_samples, batch=4096):
 
     while len(covered) < ncls and drawn < max_samples:
         b = min(batch, max_samples - drawn)
-        cls = T.sample(h, seed, drawn, b, unrooted=cur)[3]
+        cls = T.sample(h, seed, (cur << 40) + n[cur], b, unrooted=cur)[3]
         for q in range(b):
             i = int(cls[q])
             n[cur] += 1
@@ -135,3 +135,13 @@ def test_ags_switch_sequence_equals_exact_replay(oracle, k, n, deg, gseed, cbar)
     assert mut[:, 0].any(), "dropping 1/t_j would choose the same treelets"
     assert mut[:, 1].any(), "summing over uncovered graphlets would choose the same treelets"
     assert mut[:, 2].any(), "ties towards the larger j would choose the same treelets"
+
+
+def test_ags_sample_budget_fits_the_index_streams(oracle):
+    # each treelet's stream holds 2^40 indices, so a larger budget is refused
+    g = synth.erdos_renyi(16, 4.0, seed=0)
+    colors = synth.balanced_colors(g.n, 4, seed=0)
+    T = oracle.Tables(g, colors, 4, 64)
+    with pytest.raises(Exception):
+        T.estimate_ags(4, seed=1, max_samples=(1 << 40) + 1, cbar=20)
+    T.estimate_ags(4, seed=1, max_samples=1000, cbar=20)
