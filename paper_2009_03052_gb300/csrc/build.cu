@@ -338,6 +338,39 @@ __global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ 
     if (ovf) atomicOr(err, ERR_OVERFLOW);
 }
 
+// The rooted shapes of each unrooted treelet at one level: treelet j owns
+// shape[off[j] .. off[j + 1]).
+struct TreeletShapes {
+    int16_t off[32];
+    uint8_t shape[128];
+};
+
+// Per node and unrooted treelet T_j: the sum of the node's level-h counts
+// over the rooted shapes of T_j and all colour sets, tot[j * n + v].  One
+// thread per (node, treelet), treelet fastest, so a warp reads a few whole
+// rows.  Overflow of a sum is flagged.
+template <typename CT>
+__global__ void __launch_bounds__(256) treelet_totals_kernel(const CT *__restrict__ c, int64_t n, int W, int R, int Bc,
+                                                             int nu, const __grid_constant__ TreeletShapes ts,
+                                                             u128 *__restrict__ tot, int *err)
+{
+    bool ovf = false;
+    const int64_t total = n * nu;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / nu;
+        const int j = (int)(i - v * nu);
+        const CT *row = c + v * W;
+        u128 s = 0;
+        for (int q = ts.off[j]; q < ts.off[j + 1]; ++q) {
+            const int sh = ts.shape[q];
+            for (int b = 0; b < Bc; ++b) ovf |= add_ovf(s, widen(row[b * R + sh]));
+        }
+        tot[(int64_t)j * n + v] = s;
+    }
+    if (ovf) atomicOr(err, ERR_OVERFLOW);
+}
+
 constexpr int SCAN_THREADS = 512, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ u128 block_exclusive_scan(u128 x, u128 *smem, u128 &block_total)
@@ -723,6 +756,33 @@ void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allo
         launch_row_totals_t<uint64_t>((const uint64_t *)t->c[h], n, W, R, allow0, allow1, tot, err, s);
     else
         launch_row_totals_t<u128>((const u128 *)t->c[h], n, W, R, allow0, allow1, tot, err, s);
+}
+
+// Dense tables: tot[j * n + v] for every unrooted treelet j of level h in
+// one pass over the level's c rows.
+void launch_treelet_totals(const mc_tables *t, int h, u128 *tot, int *err, cudaStream_t s)
+{
+    const int64_t n = t->g->n;
+    const ShapeCatalog &cat = shape_catalog();
+    const int nu = cat.n_unrooted[h], R = cat.r[h];
+    if (n == 0 || nu == 0) return;
+    MC_REQUIRE(!t->packed, "treelet totals read dense tables");
+    TreeletShapes ts{};
+    int q = 0;
+    for (int j = 0; j < nu; ++j) {
+        ts.off[j] = (int16_t)q;
+        for (int i = 0; i < R; ++i)
+            if (cat.shapes[cat.gid(h, i)].unrooted == j) ts.shape[q++] = (uint8_t)i;
+    }
+    ts.off[nu] = (int16_t)q;
+    const int W = t->geo.Wc[h], Bc = t->geo.Bc[h];
+    const int grid = grid_for(n * nu, 256);
+    if (t->bits == 64)
+        MC_LAUNCH("treelet_totals", s, treelet_totals_kernel<uint64_t><<<grid, 256, 0, s>>>(
+                                           (const uint64_t *)t->c[h], n, W, R, Bc, nu, ts, tot, err));
+    else
+        MC_LAUNCH("treelet_totals", s, treelet_totals_kernel<u128><<<grid, 256, 0, s>>>(
+                                           (const u128 *)t->c[h], n, W, R, Bc, nu, ts, tot, err));
 }
 
 static const char *const kGatherName[MAXK + 1] = {"gather_h0", "gather_h1", "gather_h2", "gather_h3",

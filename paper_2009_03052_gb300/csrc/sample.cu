@@ -290,6 +290,30 @@ ClassCatalog *class_catalog_sigma(int h)
 // The h leaves of the decomposition are the sample's nodes; their induced
 // subgraph is classified by the lookup table.
 // ---------------------------------------------------------------------------
+// Page-locked host memory (so device-to-host copies run asynchronously)
+// and a CUDA event, released with their scope.
+template <typename T> struct Pinned {
+    T *p = nullptr;
+    explicit Pinned(size_t count)
+    {
+        if (cudaMallocHost((void **)&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(MC_E_NOMEM, "page-locked host allocation failed");
+        }
+    }
+    ~Pinned() { cudaFreeHost(p); }
+    Pinned(const Pinned &) = delete;
+    Pinned &operator=(const Pinned &) = delete;
+};
+
+struct EventHandle {
+    cudaEvent_t e = nullptr;
+    EventHandle() { MC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)); }
+    ~EventHandle() { cudaEventDestroy(e); }
+    EventHandle(const EventHandle &) = delete;
+    EventHandle &operator=(const EventHandle &) = delete;
+};
+
 // One treelet's part of a launch that draws from several treelets: samples
 // [end of the previous part, end) come from this root index, the first with
 // sample index first_index.
@@ -1016,6 +1040,7 @@ struct RootIndex {
 
 void launch_row_totals(const mc_tables *t, int h, uint64_t allow0, uint64_t allow1, u128 *tot, int *err,
                        cudaStream_t s);
+void launch_treelet_totals(const mc_tables *t, int h, u128 *tot, int *err, cudaStream_t s);
 void build_buckets(const u128 *prefix, int64_t n, int64_t nb, u128 *dD, uint32_t *start, cudaStream_t s);
 int64_t bucket_count(int64_t n);
 
@@ -1069,6 +1094,48 @@ static RootIndex root_index(const mc_tables *t, int h, int unrooted, Arena &scra
     ri.bucket = bk;
     restrict_range(ri, n, lo, hi, s);
     return ri;
+}
+
+// The root index of every unrooted treelet of level h (what root_index gives
+// for each j), with dense tables from one pass over the level's rows and one
+// synchronisation.
+static std::vector<RootIndex> treelet_root_indexes(const mc_tables *t, int h, Arena &scratch, int *err,
+                                                   cudaStream_t s,
+                                                   std::vector<std::pair<uint64_t, uint64_t>> &allows,
+                                                   int64_t lo, int64_t hi)
+{
+    const ShapeCatalog &cat = shape_catalog();
+    const int nu = cat.n_unrooted[h];
+    std::vector<RootIndex> ris((size_t)nu);
+    allows.assign((size_t)nu, {0, 0});
+    if (t->packed) {
+        for (int j = 0; j < nu; ++j)
+            ris[j] = root_index(t, h, j, scratch, err, s, allows[j].first, allows[j].second, lo, hi);
+        return ris;
+    }
+    for (int i = 0; i < cat.r[h]; ++i) {
+        auto &al = allows[(size_t)cat.shapes[cat.gid(h, i)].unrooted];
+        if (i < 64) al.first |= 1ull << i; else al.second |= 1ull << (i - 64);
+    }
+    const int64_t n = t->g->n;
+    u128 *p = scratch.get<u128>((size_t)n * nu);
+    u128 *dD = scratch.get<u128>((size_t)nu);
+    launch_treelet_totals(t, h, p, err, s);
+    for (int j = 0; j < nu; ++j) {
+        u128 *pj = p + (size_t)j * n;
+        uint32_t *bk = scratch.get<uint32_t>((size_t)t->nbucket + 1);
+        inclusive_scan_u128(pj, n, err, scratch, s);
+        build_buckets(pj, n, t->nbucket, dD + j, bk, s);
+        if (n) {
+            MC_CUDA(cudaMemcpyAsync(&ris[j].R, pj + (n - 1), sizeof(u128), cudaMemcpyDeviceToHost, s));
+            MC_CUDA(cudaMemcpyAsync(&ris[j].D, dD + j, sizeof(u128), cudaMemcpyDeviceToHost, s));
+        }
+        ris[j].prefix = pj;
+        ris[j].bucket = bk;
+    }
+    MC_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < nu; ++j) restrict_range(ris[j], n, lo, hi, s);
+    return ris;
 }
 
 static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
@@ -1519,14 +1586,14 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
         } else {
             // Algorithm AGS.  Every treelet T_j has its own stream of sample
             // indices (the n-th sample drawn with T_j has index first_index +
-            // j * 2^40 + n), so samples can be drawn ahead: a refill launch
-            // draws a run for the current treelet and a short run for every
-            // other treelet whose queue is empty, and the host replays the
+            // j * 2^40 + n), so samples can be drawn ahead: a launch draws a
+            // run for the current treelet and a short run for every other
+            // treelet whose queue is empty, and the host replays the
             // algorithm one sample at a time, taking each from the queue of
-            // the treelet it has chosen, and comes back to the GPU only when
-            // that queue runs dry.  The outcome is the one of drawing one
-            // sample at a time; what is left in the queues at the end was
-            // drawn ahead and not used.
+            // the treelet it has chosen.  One launch stays in flight while
+            // the host replays, so drawing and replaying overlap.  The
+            // outcome is the one of drawing one sample at a time; what is
+            // left in the queues at the end was drawn ahead and not used.
             int64_t cbar = p->cbar;
             if (cbar <= 0) {
                 MC_REQUIRE(p->eps > 0 && p->delta > 0 && p->delta < 1, "AGS needs cbar or (eps, delta)");
@@ -1536,12 +1603,11 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             const int nu = cat.n_unrooted[h];
             std::vector<u128> tj(nu);
             std::vector<double> tjd(nu);
-            std::vector<RootIndex> ris(nu);
-            std::vector<std::pair<uint64_t, uint64_t>> allows(nu);
+            std::vector<std::pair<uint64_t, uint64_t>> allows;
             // every treelet's root index once: its rooted total gives t_j
+            const std::vector<RootIndex> ris =
+                treelet_root_indexes(t, h, scratch, err + 1, s, allows, p->node_lo, p->node_hi);
             for (int j = 0; j < nu; ++j) {
-                ris[j] = root_index(t, h, j, scratch, err + 1, s, allows[j].first, allows[j].second, p->node_lo,
-                                    p->node_hi);
                 tj[j] = unrooted_from_rooted(t, h, j, ris[j].R);
                 tjd[j] = (double)tj[j];
             }
@@ -1553,19 +1619,29 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             std::vector<double> w((size_t)ncls, 0.0);
             std::vector<uint8_t> covered((size_t)ncls, 0);
             int64_t drawn = 0, ncov = 0;
-            // run lengths: the current treelet's first refill, its largest,
-            // and the short run drawn ahead for the others
+            // run lengths: the current treelet's first run, its largest, and
+            // the short run drawn ahead for the others
             const int64_t bmin = p->batch > 0 ? p->batch : 65536;
             const int64_t bmax = p->batch > 0 ? p->batch : (int64_t)1 << 22;
             const int64_t ahead = std::min<int64_t>(bmax, 4096);
             const int64_t cap = bmax + (int64_t)nu * ahead;  // samples of one launch, at most
             int32_t *dcls = scratch.get<int32_t>((size_t)cap);
             SampleSeg *dseg = scratch.get<SampleSeg>((size_t)nu);
-            std::vector<int32_t> hcls((size_t)cap);
-            std::vector<SampleSeg> hseg((size_t)nu);
+            Pinned<int32_t> hcls((size_t)cap);
+            Pinned<SampleSeg> hseg((size_t)nu);
+            EventHandle done;
             std::vector<std::vector<int32_t>> queue((size_t)nu);  // drawn, not yet used, in index order
             std::vector<size_t> qpos((size_t)nu, 0);
-            std::vector<int64_t> queued(nu, 0), last(nu, 0);   // samples drawn with T_j; its last run
+            std::vector<int64_t> queued(nu, 0);  // samples drawn with T_j
+            std::vector<int64_t> amount(nu, 0);                // the launch in flight, per treelet
+            int streak = 0;  // launches since the current treelet was chosen
+            bool in_flight = false;
+            unsigned long long *bytes = nullptr;
+            struct Drain {  // an error leaves no copy running into the buffers above
+                const bool &f;
+                cudaEvent_t e;
+                ~Drain() { if (f) cudaEventSynchronize(e); }
+            } drain{in_flight, done.e};
             auto weights = [&] {
                 for (int i = 0; i < ncls; ++i) {
                     double acc = 0.0;
@@ -1589,31 +1665,39 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 }
                 return best < 0.0 ? -1 : (int64_t)best;
             };
-            auto refill = [&] {
-                std::vector<int64_t> amount(nu, 0);
+            auto left = [&](int j) { return (int64_t)(queue[j].size() - qpos[j]); };
+            // plan and launch the next draw (nothing if nothing is wanted)
+            auto issue = [&] {
+                int64_t total = 0;
                 for (int j = 0; j < nu; ++j) {
-                    if (tj[j] == 0 || qpos[j] < queue[j].size()) continue;
+                    amount[j] = 0;
+                    if (tj[j] == 0) continue;
+                    const int64_t budget = p->samples - drawn - left(j);  // what T_j could still use
+                    if (budget <= 0) continue;
                     if (j == cur) {
                         int64_t want = bmin;
                         if (p->batch <= 0) {
-                            const int64_t q = predict(j);
+                            const int64_t q = predict(j) - left(j);
                             if (q >= 0) want = std::max<int64_t>(want, q + q / 4 + 4096);
-                            if (last[j] >= bmin) want = std::max(want, 2 * last[j]);  // its last run was used up
+                            // runs double while the treelet stays chosen
+                            want = std::max(want, bmin << std::min(streak, 6));
                         }
-                        amount[j] = std::min(std::min(want, bmax), p->samples - drawn);
-                    } else {
-                        amount[j] = ahead;
+                        amount[j] = std::min(std::min(want, bmax), budget);
+                    } else if (left(j) == 0) {
+                        amount[j] = std::min(ahead, budget);
                     }
+                    total += amount[j];
                 }
-                int nseg = 0;
-                int64_t total = 0;
+                if (total == 0) return;
                 SampleArgs a;
                 fill_sample_args(a, t, h);
+                int nseg = 0;
+                int64_t end = 0;
                 for (int j = 0; j < nu; ++j) {
-                    if (amount[j] <= 0) continue;
-                    SampleSeg &sg = hseg[(size_t)nseg++];
-                    total += amount[j];
-                    sg.end = total;
+                    if (amount[j] == 0) continue;
+                    SampleSeg &sg = hseg.p[nseg++];
+                    end += amount[j];
+                    sg.end = end;
                     sg.first_index = p->first_index + ((uint64_t)j << 40) + (uint64_t)queued[j];
                     sg.prefix = ris[j].prefix;
                     sg.bucket = ris[j].bucket;
@@ -1622,9 +1706,10 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     sg.D = ris[j].D;
                     sg.allow0 = allows[j].first;
                     sg.allow1 = allows[j].second;
-                    if (ris[j].R + ris[j].base > a.R + a.Xbase) { a.R = ris[j].R; a.Xbase = ris[j].base; }  // for the width test
+                    queued[j] += amount[j];
+                    if (ris[j].R + ris[j].base > a.R + a.Xbase) { a.R = ris[j].R; a.Xbase = ris[j].base; }  // width test
                 }
-                MC_CUDA(cudaMemcpyAsync(dseg, hseg.data(), (size_t)nseg * sizeof(SampleSeg), cudaMemcpyHostToDevice, s));
+                MC_CUDA(cudaMemcpyAsync(dseg, hseg.p, (size_t)nseg * sizeof(SampleSeg), cudaMemcpyHostToDevice, s));
                 a.seg = dseg;
                 a.nseg = nseg;
                 a.seed = p->seed;
@@ -1633,21 +1718,28 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.classes = dcls;
                 a.ncls = ncls;
                 a.err = err;
-                a.bytes = sample_byte_counter(scratch, s);
+                a.bytes = bytes = sample_byte_counter(scratch, s);
                 launch_sampler(t, a, s);
-                report_sample_bytes(a.bytes, s);
-                MC_CUDA(cudaMemcpyAsync(hcls.data(), dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
-                MC_CUDA(cudaStreamSynchronize(s));
+                MC_CUDA(cudaMemcpyAsync(hcls.p, dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaEventRecord(done.e, s));
+                in_flight = true;
                 st.batches++;
+            };
+            // wait for the launch in flight and append its samples to the queues
+            auto collect = [&] {
+                MC_CUDA(cudaEventSynchronize(done.e));
+                report_sample_bytes(bytes, s);
                 int64_t off = 0;
                 for (int j = 0; j < nu; ++j) {
-                    if (amount[j] <= 0) continue;
-                    queue[j].assign(hcls.begin() + off, hcls.begin() + off + amount[j]);
+                    if (amount[j] == 0) continue;
+                    std::vector<int32_t> &qj = queue[j];
+                    qj.erase(qj.begin(), qj.begin() + (std::ptrdiff_t)qpos[j]);
                     qpos[j] = 0;
-                    queued[j] += amount[j];
-                    last[j] = amount[j];
+                    qj.insert(qj.end(), hcls.p + off, hcls.p + off + amount[j]);
                     off += amount[j];
+                    amount[j] = 0;
                 }
+                in_flight = false;
             };
             int64_t target = ncls;  // round-skipped: the graphlets only stars span are left to the stars
             if (skipped) {
@@ -1655,15 +1747,34 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 for (int i = 0; i < ncls; ++i) target += sig_prime[(size_t)i] > 0;
             }
             while (cur >= 0 && ncov < target && drawn < p->samples) {
-                if (qpos[cur] == queue[cur].size()) refill();
-                const int i = queue[cur][qpos[cur]++];
-                if (i < 0 || i >= ncls) throw Error(MC_E_INTERNAL, "AGS: bad class id");
-                nj[cur]++;
-                drawn++;
-                hv[(size_t)i]++;
-                hj[(size_t)cur * ncls + i]++;
-                if ((int64_t)hv[(size_t)i] == cbar && !covered[(size_t)i]) {
-                    covered[(size_t)i] = 1;
+                if (left(cur) == 0) {
+                    if (in_flight) collect();
+                    if (left(cur) == 0) {  // the launch in flight had nothing for T_j
+                        issue();
+                        collect();
+                    }
+                    issue();  // the next draw runs while the host replays
+                    ++streak;
+                }
+                // replay until the queue runs dry, the budget ends or a
+                // graphlet becomes covered
+                const int32_t *qd = queue[cur].data();
+                const size_t q0 = qpos[cur];
+                const size_t qe = q0 + (size_t)std::min<int64_t>(left(cur), p->samples - drawn);
+                uint64_t *hjc = &hj[(size_t)cur * ncls];
+                size_t q = q0;
+                int hit = -1;
+                while (q < qe) {
+                    const int32_t i = qd[q++];
+                    if ((uint32_t)i >= (uint32_t)ncls) throw Error(MC_E_INTERNAL, "AGS: bad class id");
+                    hjc[i]++;
+                    if (++hv[(size_t)i] == (uint64_t)cbar && !covered[(size_t)i]) { hit = i; break; }
+                }
+                nj[cur] += (int64_t)(q - q0);
+                drawn += (int64_t)(q - q0);
+                qpos[cur] = q;
+                if (hit >= 0) {
+                    covered[(size_t)hit] = 1;
                     ncov++;
                     st.switches++;
                     weights();
@@ -1678,10 +1789,12 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                         const double val = acc / tjd[j];
                         if (best < 0 || val < bestv) { best = j; bestv = val; }
                     }
+                    if (best != cur) streak = 0;
                     cur = best;
                 }
             }
-            for (int j = 0; j < nu; ++j) st.discarded += (int64_t)(queue[j].size() - qpos[j]);
+            if (in_flight) collect();
+            for (int j = 0; j < nu; ++j) st.discarded += left(j);
             weights();
             for (int i = 0; i < ncls; ++i) {
                 hits[i] = hv[(size_t)i];
