@@ -527,6 +527,46 @@ __device__ __forceinline__ void adjacent4(const int64_t *row_ptr, const uint32_t
     for (int i = 0; i < NQ; ++i) out[i] = i < nq && lo[i] < end[i] && col[lo[i]] == key[i];
 }
 
+// The same tests for pairs of a sample's nodes whose adjacency offsets
+// (rlo, degree rdg) were loaded once per node: qa, qb index nodes[].
+template <int NQ, bool CNT>
+__device__ __forceinline__ void adjacent_nodes(const uint32_t *col, const int64_t *rlo, const uint32_t *rdg,
+                                               const uint32_t *nodes, const uint32_t *qa, const uint32_t *qb,
+                                               int nq, bool *out, uint64_t &rb, uint64_t &rs)
+{
+    int64_t lo[NQ], hi[NQ], end[NQ];
+    uint32_t key[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        if (i < nq) {
+            uint32_t x = qa[i], y = qb[i];
+            if (rdg[y] < rdg[x]) { const uint32_t t = x; x = y; y = t; }
+            lo[i] = rlo[x];
+            hi[i] = lo[i] + rdg[x];
+            end[i] = hi[i];
+            key[i] = nodes[y];
+            MC_COUNT(4, 32);  // the final probe
+        } else {
+            lo[i] = hi[i] = end[i] = 0;
+            key[i] = 0;
+        }
+    }
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i)
+            if (lo[i] < hi[i]) {
+                const int64_t mid = (lo[i] + hi[i]) >> 1;
+                if (col[mid] < key[i]) lo[i] = mid + 1; else hi[i] = mid;
+                MC_COUNT(4, 32);
+                more |= lo[i] < hi[i];
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) out[i] = i < nq && lo[i] < end[i] && col[lo[i]] == key[i];
+}
+
 // Lane-per-sample sampler: the 32 lanes of a warp draw 32 samples and walk
 // their h-1 decomposition steps in lockstep (every h-treelet has h-1 internal
 // decomposition nodes).  A lane does its own scalar work, short scans and
@@ -771,16 +811,23 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
                 known |= 1u << pair_pos(h, i, j);
             }
             word = known;
+            int64_t rlo[MAXK];  // adjacency offsets and degrees, loaded once per node
+            uint32_t rdg[MAXK];
+            for (int i = 0; i < h; ++i) {
+                rlo[i] = a.row_ptr[nodes[i]];
+                rdg[i] = (uint32_t)(a.row_ptr[nodes[i] + 1] - rlo[i]);
+                MC_COUNT(16, 32);
+            }
             uint32_t qa[NQ], qb[NQ];
             int qp[NQ], nq = 0;
             for (int p = 0; p < P; ++p) {
                 const int i = a.pi[p], j = a.pj[p];
                 const int bit = pair_pos(h, i, j);
                 if ((known >> bit) & 1u) continue;
-                qa[nq] = nodes[i]; qb[nq] = nodes[j]; qp[nq] = bit; ++nq;
+                qa[nq] = i; qb[nq] = j; qp[nq] = bit; ++nq;
                 if (nq == NQ || p == P - 1) {
                     bool r4[NQ];
-                    adjacent4<NQ, CNT>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
+                    adjacent_nodes<NQ, CNT>(a.col, rlo, rdg, nodes, qa, qb, nq, r4, rb, rs);
                     for (int t = 0; t < nq; ++t)
                         if (r4[t]) word |= 1u << qp[t];
                     nq = 0;
@@ -788,7 +835,7 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
             }
             if (nq) {
                 bool r4[NQ];
-                adjacent4<NQ, CNT>(a.row_ptr, a.col, qa, qb, nq, r4, rb, rs);
+                adjacent_nodes<NQ, CNT>(a.col, rlo, rdg, nodes, qa, qb, nq, r4, rb, rs);
                 for (int t = 0; t < nq; ++t)
                     if (r4[t]) word |= 1u << qp[t];
             }
