@@ -1689,13 +1689,15 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 cudaEvent_t e;
                 ~Drain() { if (f) cudaEventSynchronize(e); }
             } drain{in_flight, done.e};
+            std::vector<int> cov_list;  // covered graphlets, ascending
+            auto weight = [&](int i) {
+                double acc = 0.0;
+                for (int j = 0; j < nu; ++j)
+                    if (tj[j] > 0) acc += (double)(nj[j] * cc->sigma_ij[(size_t)i * nu + j]) / tjd[j];
+                w[(size_t)i] = acc;
+            };
             auto weights = [&] {
-                for (int i = 0; i < ncls; ++i) {
-                    double acc = 0.0;
-                    for (int j = 0; j < nu; ++j)
-                        if (tj[j] > 0) acc += (double)(nj[j] * cc->sigma_ij[(size_t)i * nu + j]) / tjd[j];
-                    w[i] = acc;
-                }
+                for (int i = 0; i < ncls; ++i) weight(i);
             };
             // Run lengths only (the outcome does not depend on them): hits per
             // class among the samples used from each T_j predict how many more
@@ -1822,17 +1824,20 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 qpos[cur] = q;
                 if (hit >= 0) {
                     covered[(size_t)hit] = 1;
+                    cov_list.insert(std::lower_bound(cov_list.begin(), cov_list.end(), hit), hit);
                     ncov++;
                     st.switches++;
-                    weights();
+                    // the choice reads w_i of the covered graphlets only: the
+                    // same sums, in the same order, over the covered list
+                    // (ascending) instead of every class
+                    for (const int i : cov_list) weight(i);
                     int best = -1;
                     double bestv = 0.0;
                     for (int j = 0; j < nu; ++j) {
                         if (tj[j] == 0) continue;
                         double acc = 0.0;
-                        for (int a2 = 0; a2 < ncls; ++a2)
-                            if (covered[(size_t)a2])
-                                acc += ((double)cc->sigma_ij[(size_t)a2 * nu + j] * (double)hv[(size_t)a2]) / w[(size_t)a2];
+                        for (const int a2 : cov_list)
+                            acc += ((double)cc->sigma_ij[(size_t)a2 * nu + j] * (double)hv[(size_t)a2]) / w[(size_t)a2];
                         const double val = acc / tjd[j];
                         if (best < 0 || val < bestv) { best = j; bestv = val; }
                     }
