@@ -363,6 +363,8 @@ struct SampleArgs {
     int32_t *shapes, *classes;
     unsigned long long *hist;
     unsigned long long *bytes;  // when set: data bytes read and written, counted item by item
+    unsigned long long *next;   // when set: warps take batches of 32 samples from this counter
+                                // (zero at launch) as they finish; else a fixed grid stride
     int ncls;
     int *err;
 };
@@ -602,7 +604,16 @@ __global__ void __launch_bounds__(256, LAT ? 1 : (sizeof(CT) == 16 ? 4 : 6))
     const int CB = (int)sizeof(CT);
     bool bad = false;
     uint64_t rb = 0, rs = 0;  // byte counts (CNT): data items, 32-byte sectors
-    for (int64_t base = warp * 32; base < a.count; base += nwarps * 32) {
+    // a warp's next batch of 32 samples: from the shared counter (the warps
+    // that draw cheap samples take more batches, so they end together), or
+    // every nwarps-th batch
+    auto take = [&](int64_t after) -> int64_t {
+        if (!a.next) return after < 0 ? warp * 32 : after + nwarps * 32;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(a.next, 32ull);
+        return (int64_t)__shfl_sync(0xffffffffu, b, 0);
+    };
+    for (int64_t base = take(-1); base < a.count; base = take(base)) {
         const int64_t sid = base + lane;
         bool ok = sid < a.count;
         uint64_t index = a.first_index + (uint64_t)sid;
@@ -1226,6 +1237,14 @@ static void launch_sampler(const mc_tables *t, SampleArgs &a, cudaStream_t s)
     MC_LAUNCH("sample", s, kern<<<(unsigned)grid, block, smem, s>>>(a));
 }
 
+// The sampler's batch counter, zeroed on the stream.
+static unsigned long long *batch_counter(Arena &scratch, cudaStream_t s)
+{
+    unsigned long long *c = scratch.get<unsigned long long>(1);
+    MC_CUDA(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
+    return c;
+}
+
 // While profiling is on, the sampler counts the bytes of the data items it
 // reads and writes into a device counter from `scratch`; the count is added
 // to the profile after the launch (one more synchronisation).
@@ -1395,6 +1414,7 @@ extern "C" mc_status mc_sample_range(const mc_tables *t, int h, int32_t unrooted
         a.ncls = (int)cc->codes.size();
         a.err = err;
         a.bytes = sample_byte_counter(scratch, s);
+        a.next = batch_counter(scratch, s);
         launch_sampler(t, a, s);
         report_sample_bytes(a.bytes, s);
         int herr[2] = {0, 0};
@@ -1615,6 +1635,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             a.ncls = ncls;
             a.err = err;
             a.bytes = sample_byte_counter(scratch, s);
+            a.next = batch_counter(scratch, s);
             launch_sampler(t, a, s);
             report_sample_bytes(a.bytes, s);
             const u128 tnum = skipped ? ri.R : ri.R / (u128)t->copies_div(h);
@@ -1768,6 +1789,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.ncls = ncls;
                 a.err = err;
                 a.bytes = bytes = sample_byte_counter(scratch, s);
+                a.next = batch_counter(scratch, s);
                 launch_sampler(t, a, s);
                 MC_CUDA(cudaMemcpyAsync(hcls.p, dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
                 MC_CUDA(cudaEventRecord(done.e, s));
