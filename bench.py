@@ -813,10 +813,12 @@ def run_serve(args):
 # profiles/), with a hash of the kernel's source file when it was captured:
 # the figure is reported only while that source is unchanged.
 TRAFFIC: dict = {
-    # profiles/gather_kernel_chung_lu_1m_k5.md, all three captured under schedule 4
-    ("chung_lu_1m_k5", "gather_h2"): (407_757_568, "887df3f50aaa2286", 4),
-    ("chung_lu_1m_k5", "gather_h3"): (1_255_241_216, "887df3f50aaa2286", 4),
-    ("chung_lu_1m_k5", "gather_h4"): (1_106_222_592, "887df3f50aaa2286", 4),
+    # profiles/sample_kernel_chung_lu_1m_k5.md
+    ("chung_lu_1m_k5", "sample"): (2_769_788_160, "eda66c083c84b016"),
+    # profiles/gather_kernel_chung_lu_1m_k5.md, under schedules 6, 4, 4
+    ("chung_lu_1m_k5", "gather_h2"): (547_624_704, "887df3f50aaa2286", 6),
+    ("chung_lu_1m_k5", "gather_h3"): (1_255_503_360, "887df3f50aaa2286", 4),
+    ("chung_lu_1m_k5", "gather_h4"): (1_106_538_496, "887df3f50aaa2286", 4),
 }
 KERNEL_SOURCE = {"sample": "sample.cu", "gather": "gather.cuh", "merge": "build.cu"}
 
