@@ -323,10 +323,17 @@ __global__ void __launch_bounds__(256) row_totals_kernel(const CT *__restrict__ 
         const int64_t v = v0 + grp;
         u128 s = 0;
         if (v < n)
-            for (int e = j; e < W; e += G) {
-                const int sh = e % R;  // set-major row: entry e is (set e / R, shape e % R)
-                const bool ok = sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1;
-                if (ok) ovf |= add_ovf(s, widen(c[v * W + e]));
+            for (int eb = j; eb < W; eb += 8 * G) {  // up to 8 loads in flight per lane
+                CT x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int e = eb + i * G;
+                    const int sh = e % R;  // set-major row: entry e is (set e / R, shape e % R)
+                    const bool ok = e < W && (sh < 64 ? (allow0 >> sh) & 1 : (allow1 >> (sh - 64)) & 1);
+                    x[i] = ok ? c[v * W + e] : (CT)0;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) ovf |= add_ovf(s, widen(x[i]));
             }
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) {
@@ -729,8 +736,8 @@ template <typename CT>
 static void launch_row_totals_t(const CT *c, int64_t n, int W, int R, uint64_t allow0, uint64_t allow1, u128 *tot,
                                 int *err, cudaStream_t s)
 {
-    int G = 1;
-    while (G < W && G < 32) G <<= 1;
+    int G = 1;  // lanes per node: each covers up to 8 entries
+    while (G * 8 < W && G < 32) G <<= 1;
     const int grid = grid_for((n * G + 31) / 32 * 32, 256);
     switch (G) {
     case 1: MC_LAUNCH("row_totals", s, row_totals_kernel<CT, 1><<<grid, 256, 0, s>>>(c, n, W, R, allow0, allow1, tot, err)); break;
