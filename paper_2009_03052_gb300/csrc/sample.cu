@@ -290,21 +290,32 @@ ClassCatalog *class_catalog_sigma(int h)
 // The h leaves of the decomposition are the sample's nodes; their induced
 // subgraph is classified by the lookup table.
 // ---------------------------------------------------------------------------
-// Page-locked host memory (so device-to-host copies run asynchronously)
-// and a CUDA event, released with their scope.
-template <typename T> struct Pinned {
-    T *p = nullptr;
-    explicit Pinned(size_t count)
-    {
-        if (cudaMallocHost((void **)&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+// Page-locked host memory (so device-to-host copies run asynchronously),
+// one buffer per calling thread, grown on demand and kept for the thread's
+// next calls: page-locking is slow, and a thread runs one call at a time.
+static void *pinned_scratch(size_t bytes)
+{
+    struct Buf {
+        void *p = nullptr;
+        size_t n = 0;
+        ~Buf() { if (p) cudaFreeHost(p); }
+    };
+    thread_local Buf b;
+    if (b.n < bytes) {
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        if (cudaMallocHost(&b.p, bytes) != cudaSuccess) {
             cudaGetLastError();
+            b.p = nullptr;
             throw Error(MC_E_NOMEM, "page-locked host allocation failed");
         }
+        b.n = bytes;
     }
-    ~Pinned() { cudaFreeHost(p); }
-    Pinned(const Pinned &) = delete;
-    Pinned &operator=(const Pinned &) = delete;
-};
+    return b.p;
+}
+
+// A CUDA event, released with its scope.
 
 struct EventHandle {
     cudaEvent_t e = nullptr;
@@ -1695,8 +1706,11 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
             const int64_t cap = bmax + (int64_t)nu * ahead;  // samples of one launch, at most
             int32_t *dcls = scratch.get<int32_t>((size_t)cap);
             SampleSeg *dseg = scratch.get<SampleSeg>((size_t)nu);
-            Pinned<int32_t> hcls((size_t)cap);
-            Pinned<SampleSeg> hseg((size_t)nu);
+            // the part table, then the class ids of one launch
+            const size_t seg_bytes = ((size_t)nu * sizeof(SampleSeg) + 255) & ~(size_t)255;
+            char *pin = (char *)pinned_scratch(seg_bytes + (size_t)cap * sizeof(int32_t));
+            SampleSeg *hseg = (SampleSeg *)pin;
+            int32_t *hcls = (int32_t *)(pin + seg_bytes);
             EventHandle done;
             std::vector<std::vector<int32_t>> queue((size_t)nu);  // drawn, not yet used, in index order
             std::vector<size_t> qpos((size_t)nu, 0);
@@ -1765,7 +1779,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 int64_t end = 0;
                 for (int j = 0; j < nu; ++j) {
                     if (amount[j] == 0) continue;
-                    SampleSeg &sg = hseg.p[nseg++];
+                    SampleSeg &sg = hseg[nseg++];
                     end += amount[j];
                     sg.end = end;
                     sg.first_index = p->first_index + ((uint64_t)j << 40) + (uint64_t)queued[j];
@@ -1779,7 +1793,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     queued[j] += amount[j];
                     if (ris[j].R + ris[j].base > a.R + a.Xbase) { a.R = ris[j].R; a.Xbase = ris[j].base; }  // width test
                 }
-                MC_CUDA(cudaMemcpyAsync(dseg, hseg.p, (size_t)nseg * sizeof(SampleSeg), cudaMemcpyHostToDevice, s));
+                MC_CUDA(cudaMemcpyAsync(dseg, hseg, (size_t)nseg * sizeof(SampleSeg), cudaMemcpyHostToDevice, s));
                 a.seg = dseg;
                 a.nseg = nseg;
                 a.seed = p->seed;
@@ -1791,7 +1805,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                 a.bytes = bytes = sample_byte_counter(scratch, s);
                 a.next = batch_counter(scratch, s);
                 launch_sampler(t, a, s);
-                MC_CUDA(cudaMemcpyAsync(hcls.p, dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
+                MC_CUDA(cudaMemcpyAsync(hcls, dcls, (size_t)total * 4, cudaMemcpyDeviceToHost, s));
                 MC_CUDA(cudaEventRecord(done.e, s));
                 in_flight = true;
                 st.batches++;
@@ -1806,7 +1820,7 @@ extern "C" mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_pa
                     std::vector<int32_t> &qj = queue[j];
                     qj.erase(qj.begin(), qj.begin() + (std::ptrdiff_t)qpos[j]);
                     qpos[j] = 0;
-                    qj.insert(qj.end(), hcls.p + off, hcls.p + off + amount[j]);
+                    qj.insert(qj.end(), hcls + off, hcls + off + amount[j]);
                     off += amount[j];
                     amount[j] = 0;
                 }
