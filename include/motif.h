@@ -328,7 +328,10 @@ typedef struct {
 
 /* est: host double[N_h], the estimated number of induced copies of each
  * h-node graphlet in G; hits: host uint64[N_h], samples per graphlet;
- * stats: host, may be NULL.  N_h = mc_num_classes(h).  Synchronises. */
+ * stats: host, may be NULL.  N_h = mc_num_classes(h).  Synchronises.  AGS
+ * page-locks a host buffer of about 4 (B + 4096 U) bytes (B = batch, or 2^22
+ * when automatic; U = mc_num_unrooted(h)) that the calling thread keeps for
+ * its later calls and frees when it exits. */
 mc_status mc_estimate_counts(const mc_tables *t, const mc_estimate_params *params, double *est,
                              uint64_t *hits, mc_estimate_stats *stats, void *stream);
 
