@@ -161,15 +161,33 @@ __global__ void degree_hist_kernel(const int64_t *__restrict__ row_ptr, int64_t 
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+// A block takes a tile of blockDim nodes at a time: shared-memory counts
+// give each node its place among the tile's nodes of its degree, one global
+// atomic per degree present reserves the tile's run in that degree's
+// bucket.  (The order inside a bucket is free: the sums are per node.)
 __global__ void degree_order_kernel(const int64_t *__restrict__ row_ptr, int64_t n, unsigned *cursor,
                                     uint4 *__restrict__ sched)
 {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e0 = row_ptr[v], d = row_ptr[v + 1] - e0;
+    __shared__ unsigned cnt[HUB_CHUNK + 1], base[HUB_CHUNK + 1];
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < n; t0 += (int64_t)gridDim.x * blockDim.x) {
+        for (int i = threadIdx.x; i <= HUB_CHUNK; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const int64_t v = t0 + threadIdx.x;
+        int64_t e0 = 0, d = HUB_CHUNK + 1;
+        if (v < n) {
+            e0 = row_ptr[v];
+            d = row_ptr[v + 1] - e0;
+        }
+        unsigned local = 0;
+        if (d <= HUB_CHUNK) local = atomicAdd(&cnt[d], 1u);
+        __syncthreads();
+        for (int i = threadIdx.x; i <= HUB_CHUNK; i += blockDim.x)
+            base[i] = cnt[i] ? atomicAdd(&cursor[i], cnt[i]) : 0u;
+        __syncthreads();
         if (d <= HUB_CHUNK)
-            sched[atomicAdd(&cursor[d], 1u)] =
+            sched[base[d] + local] =
                 make_uint4((uint32_t)v, (uint32_t)e0, (uint32_t)((uint64_t)e0 >> 32), (uint32_t)d);
+        __syncthreads();  // cnt and base are reused by the next tile
     }
 }
 
