@@ -427,7 +427,34 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
         g->row_ptr = g->arena.get<int64_t>((size_t)n + 1);
         g->col = g->arena.get<uint32_t>((size_t)(nnz > 0 ? nnz : 1));
         MC_CUDA(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int64_t) * (n + 1), kind, s));
-        if (nnz) MC_CUDA(cudaMemcpyAsync(g->col, col, sizeof(uint32_t) * nnz, kind, s));
+        // A trusted graph's ids are copied on a side stream while the
+        // degree statistics, hub chunks and schedule (which read only the
+        // offsets) run on s; s joins the copy before the load returns, and
+        // a failing load waits for it before its buffers are freed.
+        struct SideCopy {
+            cudaStream_t s2 = nullptr;
+            cudaEvent_t ready = nullptr, done = nullptr;
+            ~SideCopy()
+            {
+                if (s2) {
+                    cudaStreamSynchronize(s2);
+                    cudaStreamDestroy(s2);
+                }
+                if (ready) cudaEventDestroy(ready);
+                if (done) cudaEventDestroy(done);
+            }
+        } side;
+        if (nnz && trusted) {
+            MC_CUDA(cudaStreamCreateWithFlags(&side.s2, cudaStreamNonBlocking));
+            MC_CUDA(cudaEventCreateWithFlags(&side.ready, cudaEventDisableTiming));
+            MC_CUDA(cudaEventCreateWithFlags(&side.done, cudaEventDisableTiming));
+            MC_CUDA(cudaEventRecord(side.ready, s));  // after the allocations and the caller's work on s
+            MC_CUDA(cudaStreamWaitEvent(side.s2, side.ready, 0));
+            MC_CUDA(cudaMemcpyAsync(g->col, col, sizeof(uint32_t) * nnz, kind, side.s2));
+            MC_CUDA(cudaEventRecord(side.done, side.s2));
+        } else if (nnz) {
+            MC_CUDA(cudaMemcpyAsync(g->col, col, sizeof(uint32_t) * nnz, kind, s));
+        }
         // the offsets are checked before any kernel indexes with them: on the
         // host for host input, by a kernel (and a read-back) for device input
         if (!trusted) {
@@ -513,6 +540,7 @@ extern "C" mc_status mc_load_graph(int64_t n, int64_t nnz, const int64_t *row_pt
             MC_LAUNCH("degree_order", s, degree_order_kernel<<<grid_for(n, 256), 256, 0, s>>>(
                                              g->row_ptr, n, dh + HUB_CHUNK + 1, g->sched));
         }
+        if (side.done) MC_CUDA(cudaStreamWaitEvent(s, side.done, 0));  // the ids are in place
         MC_CUDA(cudaStreamSynchronize(s));
         g->n_big_hubs = nbig;
     });
