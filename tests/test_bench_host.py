@@ -1,6 +1,7 @@
 """Host-side pieces of the benchmark (no GPU): the entry counts behind the
 metric and the compulsory-bytes model of the build kernels."""
 import math
+import os
 
 import bench
 
@@ -61,3 +62,26 @@ def test_traffic_only_for_the_captured_source(monkeypatch):
     assert bench.traffic_of("w", "gather_h3", 4) == 7
     assert bench.traffic_of("w", "gather_h3", 6) is None
     assert bench.source_hash("gather_h3") == bench.source_hash("gather_h4") != ""
+
+
+def test_reference_arm_line_on_the_small_case():
+    # the reference arm (the oracle on host cores) prints the contract's line
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--small", "--steps", "1",
+                          "--warmup", "3"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config"):
+        assert key in line, key
+    assert line["steps"] == 1 and line["warmup"] == 3 and line["value"] > 0
+    assert line["config"]["workload"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
